@@ -1,0 +1,413 @@
+"""Pins of the FP64 CPU oracle against what the scheme and the mathematics fix
+(no GPU): hand-evaluated worked examples, closed-form coefficients, exact
+invariants of the Piacsek-Williams form (uniform flow, energy conservation,
+skew-adjointness, the momentum / divergence identity), second-order convergence
+to the continuous skew-symmetric tendency, and the adjoint by dot-product and
+brute-force tests.  A final test plants plausible mistakes in copies of the
+oracle source and checks that these pins catch every one.
+"""
+import json
+import math
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_12850_b300 import synthetic
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def unit_coeffs(nz=4):
+    return oracle.Coeffs(nz, 1.0, 1.0, dz=np.ones(nz), rho_n=np.ones(nz), rho_w=np.ones(nz), rho0=1.0)
+
+
+def grid_idx(n=4):
+    return np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+
+
+def rand_fields(rng, nx, ny, nz, lid=True):
+    u = 5 + rng.standard_normal((nx, ny, nz))
+    v = 5 + rng.standard_normal((nx, ny, nz))
+    w = 0.3 * rng.standard_normal((nx, ny, nz))
+    if lid:
+        w[:, :, -1] = 0.0
+    return u, v, w
+
+
+def stretched(nz, dx=37.0, dy=53.0):
+    return oracle.Coeffs(nz, dx, dy)
+
+
+def wdot(c, a, b, grid):
+    wuv, ww = oracle.weights(c)
+    W = wuv if grid < 2 else ww
+    return float(np.sum(W[None, None, :] * a * b))
+
+
+# --------------------------------------------------------------------------
+# pins (each returns normally or raises AssertionError)
+# --------------------------------------------------------------------------
+def pin_worked_examples():
+    spec = json.load(open(os.path.join(GOLDEN, "pw_worked_examples.json")))
+    c = unit_coeffs()
+    I, J, K = grid_idx()
+    z = np.zeros((4, 4, 4))
+    ex = {e["name"]: e["expect"] for e in spec["examples"]}
+    # E1
+    su, sv, sw = oracle.advect(c, 1.0 + I, z, z)
+    np.testing.assert_array_equal(su, np.broadcast_to(np.array(ex["E1"]["su_i"])[:, None, None], su.shape))
+    assert not sv.any() and not sw.any()
+    # E2
+    w = np.broadcast_to(np.array([1.0, 2.0, 1.0, 0.0]), (4, 4, 4)).copy()
+    su, sv, sw = oracle.advect(c, 1.0 + K, z, w)
+    np.testing.assert_array_equal(su, np.broadcast_to(np.array(ex["E2"]["su_k"]), su.shape))
+    np.testing.assert_array_equal(sw, np.broadcast_to(np.array(ex["E2"]["sw_k"]), sw.shape))
+    assert not sv.any()
+    # E3
+    su, sv, sw = oracle.advect(c, 2.0 + 0 * I, 1.0 + I, z)
+    np.testing.assert_array_equal(sv, np.broadcast_to(np.array(ex["E3"]["sv_i"])[:, None, None], sv.shape))
+    assert not su.any() and not sw.any()
+    # E4
+    w = np.zeros((4, 4, 4))
+    w[:, :, 0] = (1.0 + I)[:, :, 0]
+    su, sv, sw = oracle.advect(c, 1.0 + K, z, w)
+    np.testing.assert_array_equal(sw, np.broadcast_to(np.array(ex["E4"]["sw_ik"])[:, None, :], sw.shape))
+    np.testing.assert_array_equal(su, np.broadcast_to(np.array(ex["E4"]["su_ik"])[:, None, :], su.shape))
+    assert not sv.any()
+    # E5
+    su, sv, sw = oracle.advect(c, 1.0 + J, 1.0 + I, z)
+    np.testing.assert_array_equal(su, np.broadcast_to(np.array(ex["E5"]["su_ij"])[:, :, None], su.shape))
+    np.testing.assert_array_equal(sv, np.broadcast_to(np.array(ex["E5"]["sv_ij"])[:, :, None], sv.shape))
+    assert not sw.any()
+
+
+def pin_coefficients():
+    spec = json.load(open(os.path.join(GOLDEN, "pw_coefficients_nz3.json")))
+    c = oracle.Coeffs(3, 50.0, 50.0)
+    np.testing.assert_allclose(c.dz, spec["dz"], rtol=1e-15)
+    np.testing.assert_allclose(c.zf, spec["zf"], rtol=1e-15)
+    np.testing.assert_allclose(c.zn, spec["zn"], rtol=1e-15)
+    np.testing.assert_allclose(c.dzn[:2], spec["dzn"], rtol=1e-15)
+    for name in ("tzc1", "tzc2", "tzd1", "tzd2"):
+        want = np.array([a * math.exp(e / 8000.0) for a, e in spec[name]])
+        np.testing.assert_allclose(getattr(c, name), want, rtol=2e-15, atol=0, err_msg=name)
+    assert c.tcx == 0.25 / 50.0 and c.tcy == 0.25 / 50.0
+
+
+def pin_uniform_flow():
+    rng = np.random.default_rng(5)
+    nz = 9
+    c = oracle.Coeffs(nz, 31.0, 17.0, dz=rng.uniform(5, 50, nz), rho_n=rng.uniform(0.5, 1.5, nz),
+                      rho_w=rng.uniform(0.5, 1.5, nz))
+    U = np.full((6, 5, nz), 7.25)
+    V = np.full((6, 5, nz), -3.5)
+    W = np.zeros((6, 5, nz))
+    for s in oracle.advect(c, U, V, W):
+        assert not s.any()
+
+
+def pin_energy():
+    rng = np.random.default_rng(6)
+    for nx, ny, nz in ((7, 5, 6), (4, 9, 2), (3, 3, 1)):
+        c = stretched(nz)
+        u, v, w = rand_fields(rng, nx, ny, nz)
+        (su, sv, sw), _ = oracle.advect(c, u, v, w, want_cond=True)
+        for g, (phi, s) in enumerate(((u, su), (v, sv), (w, sw))):
+            num = wdot(c, phi, s, g)
+            den = wdot(c, np.abs(phi), np.abs(s), g)
+            assert abs(num) <= 1e-14 * den + 1e-300, (g, num, den)
+
+
+def pin_skew_adjoint():
+    rng = np.random.default_rng(7)
+    nx, ny, nz = 6, 5, 7
+    c = stretched(nz)
+    a = rand_fields(rng, nx, ny, nz)
+    for g in range(3):
+        phi = rng.standard_normal((nx, ny, nz))
+        psi = rng.standard_normal((nx, ny, nz))
+        if g == 2:
+            phi[:, :, -1] = 0.0
+            psi[:, :, -1] = 0.0
+        lhs = wdot(c, psi, oracle.src(c, g, *a, phi), g)
+        rhs = -wdot(c, oracle.src(c, g, *a, psi), phi, g)
+        scale = wdot(c, np.abs(psi), np.abs(oracle.src(c, g, *a, phi)), g)
+        assert abs(lhs - rhs) <= 1e-13 * scale, (g, lhs, rhs)
+
+
+def streamfunction_flow(rng, nx, ny, nz, dx, dy):
+    """w = 0 and (u, v) = (-d psi/dy, d psi/dx) from a corner streamfunction:
+    psi[i, j] sits at (x_{i+1/2}, y_{j+1/2}); discretely divergence-free."""
+    psi = rng.standard_normal((nx, ny, nz))
+    u = -(psi - np.roll(psi, 1, axis=1)) / dy
+    v = (psi - np.roll(psi, 1, axis=0)) / dx
+    return 5 + u, 3 + v, np.zeros((nx, ny, nz))
+
+
+def pin_momentum_divergence_free():
+    rng = np.random.default_rng(8)
+    nx, ny, nz, dx, dy = 8, 6, 5, 40.0, 60.0
+    c = stretched(nz, dx, dy)
+    u, v, w = streamfunction_flow(rng, nx, ny, nz, dx, dy)
+    # the flow really is divergence-free at every cell centre
+    div = (u - np.roll(u, 1, axis=0)) / dx + (v - np.roll(v, 1, axis=1)) / dy
+    assert np.abs(div).max() < 1e-13
+    su, sv, sw = oracle.advect(c, u, v, w)
+    assert not sw.any()
+    for g, s in ((0, su), (1, sv)):
+        tot = wdot(c, np.ones_like(s), s, g)
+        assert abs(tot) <= 1e-14 * wdot(c, np.ones_like(s), np.abs(s), g), (g, tot)
+
+
+def pin_momentum_identity():
+    rng = np.random.default_rng(9)
+    nx, ny, nz = 7, 6, 8
+    c = stretched(nz)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    s = oracle.advect(c, u, v, w)
+    for g, phi in enumerate((u, v, w)):
+        D = oracle.face_divergence(c, g, u, v, w)
+        lhs = wdot(c, np.ones_like(phi), s[g], g)
+        rhs = wdot(c, phi, D, g)
+        scale = wdot(c, np.ones_like(phi), np.abs(s[g]), g)
+        assert abs(lhs - rhs) <= 1e-13 * scale, (g, lhs, rhs)
+        assert abs(lhs) > 1e-6 * scale  # arbitrary fields: the integral does not vanish
+
+
+def continuum_fields(H):
+    import sympy as sp
+    x, y, z = sp.symbols("x y z", real=True)
+    Lx, Ly, Z = 2000.0, 1600.0, 1000.0
+    kx, ky = 2 * sp.pi / Lx, 2 * sp.pi / Ly
+    u = 3 + sp.sin(kx * x + 0.4) * sp.cos(ky * y) * (1 + 0.3 * sp.cos(sp.pi * z / Z))
+    v = 2 + sp.cos(kx * x) * sp.sin(ky * y + 0.7) * (1 + 0.2 * z / Z)
+    w = 0.5 * sp.sin(sp.pi * z / Z) * sp.cos(kx * x + 0.1) * sp.sin(ky * y + 0.2)
+    rho = 1.2 * sp.exp(-z / H)
+    div = (sp.diff(rho * u, x) + sp.diff(rho * v, y) + sp.diff(rho * w, z)) / rho
+    out = []
+    for phi in (u, v, w):
+        S = -(u * sp.diff(phi, x) + v * sp.diff(phi, y) + w * sp.diff(phi, z)) - phi * div / 2
+        out.append(sp.lambdify((x, y, z), S, "numpy"))
+    fl = [sp.lambdify((x, y, z), f, "numpy") for f in (u, v, w)]
+    return fl, out, (Lx, Ly, Z)
+
+
+def pin_continuum_second_order():
+    H = 1500.0
+    fl, Sl, (Lx, Ly, Z) = continuum_fields(H)
+    errs = []
+    for N in (12, 24, 48):
+        nx = ny = nz = N
+        dx, dy, dz = Lx / nx, Ly / ny, Z / nz
+        c = oracle.Coeffs(nz, dx, dy, dz=np.full(nz, dz), rho0=1.2, H=H)
+        i = np.arange(nx)[:, None, None]
+        j = np.arange(ny)[None, :, None]
+        zn = ((np.arange(nz) + 0.5) * dz)[None, None, :]
+        zf = ((np.arange(nz) + 1.0) * dz)[None, None, :]
+        pts = [((i + 0.5) * dx, j * dy, zn), (i * dx, (j + 0.5) * dy, zn), (i * dx, j * dy, zf)]
+        F = [np.broadcast_to(fl[q](*pts[q]), (nx, ny, nz)).astype(np.float64).copy() for q in range(3)]
+        F[2][:, :, -1] = 0.0
+        S = oracle.advect(c, *F)
+        e = 0.0
+        for q in range(3):
+            ref = np.broadcast_to(Sl[q](*pts[q]), (nx, ny, nz))
+            mask = np.ones((nx, ny, nz), bool)
+            if q == 2:
+                mask[:, :, -1] = False
+            e = max(e, float(np.abs(S[q] - ref)[mask].max() / np.abs(ref).max()))
+        errs.append(e)
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.3 < r1 < 4.8 and 3.3 < r2 < 4.8, errs
+
+
+def jvp(c, x, e):
+    """J(x) e by central difference; exact (up to rounding) since S is quadratic."""
+    p = oracle.advect(c, *(x[q] + e[q] for q in range(3)))
+    m = oracle.advect(c, *(x[q] - e[q] for q in range(3)))
+    return tuple((p[q] - m[q]) / 2 for q in range(3))
+
+
+def pin_adjoint_dot():
+    rng = np.random.default_rng(10)
+    nx, ny, nz = 6, 7, 6
+    c = stretched(nz)
+    x = rand_fields(rng, nx, ny, nz)
+    e = list(rand_fields(rng, nx, ny, nz))
+    y = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
+    Je = jvp(c, x, e)
+    JTy = oracle.adjoint(c, *x, *y)
+    lhs = sum(float(np.sum(Je[q] * y[q])) for q in range(3))
+    rhs = sum(float(np.sum(e[q] * JTy[q])) for q in range(3))
+    scale = sum(float(np.sum(np.abs(Je[q] * y[q]))) for q in range(3))
+    assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs)
+    # the lid face is not a degree of freedom
+    assert not JTy[2][:, :, -1].any()
+
+
+def pin_adjoint_bruteforce():
+    rng = np.random.default_rng(11)
+    nx, ny, nz = 3, 4, 4
+    c = stretched(nz)
+    x = rand_fields(rng, nx, ny, nz)
+    y = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
+    JTy = oracle.adjoint(c, *x, *y)
+    n = nx * ny * nz
+    for q in range(3):
+        col = np.zeros(n)
+        for m in range(n):
+            e = [np.zeros((nx, ny, nz)) for _ in range(3)]
+            e[q].reshape(-1)[m] = 1.0
+            if q == 2 and m % nz == nz - 1:
+                col[m] = 0.0          # lid value is never read
+                continue
+            Je = jvp(c, x, e)
+            col[m] = sum(float(np.sum(Je[r] * y[r])) for r in range(3))
+        np.testing.assert_allclose(JTy[q].reshape(-1), col, rtol=1e-12, atol=1e-12)
+
+
+def pin_loop_gradient():
+    rng = np.random.default_rng(12)
+    nx, ny, nz, dt, steps = 5, 4, 5, 0.5, 4
+    c = stretched(nz, 50.0, 50.0)
+    x = rand_fields(rng, nx, ny, nz)
+    L, g = oracle.loss_and_grad(c, *x, dt, steps)
+    for trial in range(8):
+        q = int(rng.integers(0, 3))
+        i, j = int(rng.integers(0, nx)), int(rng.integers(0, ny))
+        k = int(rng.integers(0, nz - 1 if q == 2 else nz))
+        fd = []
+        for h in (1e-3, 1e-4):
+            xp = [a.copy() for a in x]
+            xm = [a.copy() for a in x]
+            xp[q][i, j, k] += h
+            xm[q][i, j, k] -= h
+            Lp, _ = oracle.loss_and_grad(c, *xp, dt, steps)
+            Lm, _ = oracle.loss_and_grad(c, *xm, dt, steps)
+            fd.append((Lp - Lm) / (2 * h))
+        gv = g[q][i, j, k]
+        e1, e2 = abs(fd[0] - gv), abs(fd[1] - gv)
+        tol = 1e-7 * max(1.0, abs(gv))
+        assert e2 <= tol or e2 < e1 / 20, (q, i, j, k, gv, fd)
+
+
+def pin_cond_and_points():
+    rng = np.random.default_rng(13)
+    nx, ny, nz = 5, 6, 7
+    c = stretched(nz)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    (su, sv, sw), (cu, cv, cw) = oracle.advect(c, u, v, w, want_cond=True)
+    for s, cc in ((su, cu), (sv, cv), (sw, cw)):
+        assert np.all(np.abs(s) <= cc * (1 + 1e-15))
+    pts = np.array([[0, 0, 0], [4, 5, 6], [2, 3, 0], [1, 0, 6], [3, 2, 5]])
+    vals, cond = oracle.advect_points(c, u, v, w, pts)
+    for p, (i, j, k) in enumerate(pts):
+        assert vals[p, 0] == su[i, j, k] and vals[p, 1] == sv[i, j, k] and vals[p, 2] == sw[i, j, k]
+        assert cond[p, 0] == cu[i, j, k] and cond[p, 2] == cw[i, j, k]
+
+
+def pin_lid_ignored():
+    """The lid face w(nz-1) is 0 by definition: whatever is stored there must not
+    change any source or gradient."""
+    rng = np.random.default_rng(15)
+    nx, ny, nz = 5, 4, 6
+    c = stretched(nz)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    w2 = w.copy()
+    w2[:, :, -1] = 100.0 * rng.standard_normal((nx, ny))
+    for a, b in zip(oracle.advect(c, u, v, w), oracle.advect(c, u, v, w2)):
+        assert np.array_equal(a, b)
+    y = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
+    for a, b in zip(oracle.adjoint(c, u, v, w, *y), oracle.adjoint(c, u, v, w2, *y)):
+        assert np.array_equal(a, b)
+
+
+PINS = [pin_worked_examples, pin_lid_ignored, pin_coefficients, pin_uniform_flow, pin_energy, pin_skew_adjoint,
+        pin_momentum_divergence_free, pin_momentum_identity, pin_continuum_second_order,
+        pin_adjoint_dot, pin_adjoint_bruteforce, pin_cond_and_points]
+
+
+@pytest.mark.parametrize("pin", PINS + [pin_loop_gradient], ids=lambda f: f.__name__)
+def test_pin(pin):
+    pin()
+
+
+def test_default_stretch_and_generators():
+    dz = synthetic.default_dz(9)
+    assert dz[0] == 10.0 and abs(dz[-1] - 40.0) < 1e-12
+    assert np.allclose(dz[1:] / dz[:-1], 4 ** (1 / 8))
+    c = oracle.Coeffs(9, 50.0, 50.0)
+    np.testing.assert_allclose(c.dz, dz, rtol=1e-15)
+    u, v, w = synthetic.wind_fields(8, 8, 6, 1)
+    assert not w[:, :, -1].any()
+    u2, _, _ = synthetic.wind_fields(8, 8, 6, 1)
+    assert np.array_equal(u, u2)
+
+
+def test_residuals_match_identities():
+    rng = np.random.default_rng(14)
+    nx, ny, nz = 6, 6, 6
+    c = stretched(nz)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    s = oracle.advect(c, u, v, w)
+    (re, rm) = oracle.residuals(c, u, v, w, *s)
+    assert max(abs(r) for r in re) < 1e-14
+    assert all(abs(r) > 1e-8 for r in rm)     # arbitrary fields: momentum not conserved
+    x = streamfunction_flow(rng, nx, ny, nz, 37.0, 53.0)
+    (re2, rm2) = oracle.residuals(c, *x, *oracle.advect(c, *x))
+    assert abs(rm2[0]) < 1e-14 and abs(rm2[1]) < 1e-14 and max(abs(r) for r in re2) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: each must be caught by at least one pin
+# --------------------------------------------------------------------------
+MUTANTS = {
+    "su_x_sign": ("                - at(g, p, i + 1, j, k) * (at(g, u, i, j, k) + at(g, u, i + 1, j, k)));\n    c = fabs(g->tcx) * (fabs(at(g, p, i - 1, j, k)) * (fabs(at(g, u, i - 1, j, k)) + fabs(at(g, u, i, j, k)))",
+                  "                + at(g, p, i + 1, j, k) * (at(g, u, i, j, k) + at(g, u, i + 1, j, k)));\n    c = fabs(g->tcx) * (fabs(at(g, p, i - 1, j, k)) * (fabs(at(g, u, i - 1, j, k)) + fabs(at(g, u, i, j, k)))"),
+    "su_y_index": ("(at(g, v, i, j - 1, k) + at(g, v, i + 1, j - 1, k))\n                    - at(g, p, i, j + 1, k)",
+                   "(at(g, v, i, j - 1, k) + at(g, v, i - 1, j - 1, k))\n                    - at(g, p, i, j + 1, k)"),
+    "sv_drop_tzc2": ("        s = s - g->tzc2[k] * at(g, p, i, j, k + 1) * (at(g, w, i, j, k) + at(g, w, i, j + 1, k));",
+                     "        s = s;"),
+    "su_swap_tzc": ("        s = s + g->tzc1[k] * at(g, p, i, j, k - 1) * (at(g, w, i, j, k - 1) + at(g, w, i + 1, j, k - 1));",
+                    "        s = s + g->tzc2[k] * at(g, p, i, j, k - 1) * (at(g, w, i, j, k - 1) + at(g, w, i + 1, j, k - 1));"),
+    "tzc1_wrong_rho": ("        double rw_below = (k == 0) ? rho0 : rhow[k - 1];",
+                       "        double rw_below = (k == 0) ? rho0 : rhon[k - 1];"),
+    "tzd2_wrong_level": ("            tzd2[k] = 0.25 * rhon[k + 1] / (rhow[k] * dzn[k]);",
+                         "            tzd2[k] = 0.25 * rhon[k] / (rhow[k] * dzn[k]);"),
+    "sw_x_transposed": ("(at(g, u, i - 1, j, k) + at(g, u, i - 1, j, k + 1))\n                - at(g, p, i + 1, j, k) * (at(g, u, i, j, k) + at(g, u, i, j, k + 1)));\n    c = fabs(g->tcx) * (fabs(at(g, p, i - 1, j, k)) * (fabs(at(g, u, i - 1, j, k)) + fabs(at(g, u, i - 1, j, k + 1)))",
+                        "(at(g, u, i - 1, j, k) + at(g, u, i, j, k + 1))\n                - at(g, p, i + 1, j, k) * (at(g, u, i, j, k) + at(g, u, i, j, k + 1)));\n    c = fabs(g->tcx) * (fabs(at(g, p, i - 1, j, k)) * (fabs(at(g, u, i - 1, j, k)) + fabs(at(g, u, i - 1, j, k + 1)))"),
+    "sw_reads_lid": ("    if (k + 1 < nz - 1) {   /* phi(k+1) is the lid when k+1 = nz-1: 0 */",
+                     "    if (k < nz - 1) {   /* phi(k+1) is the lid when k+1 = nz-1: 0 */"),
+    "adjoint_table_offset": ("    {1, CX, -1, +1, 0, 0, 0, 0, 0, 0, 0, +1, 0, 0},",
+                             "    {1, CX, -1, +1, 0, 0, 0, 0, 0, 0, +1, 0, 0, 0},"),
+    "adjoint_sign": ("    {2, D2, -1, 0, 0, +1, 2, 0, 0, 0, 0, 0, +1, 3},",
+                     "    {2, D2, +1, 0, 0, +1, 2, 0, 0, 0, 0, 0, +1, 3},"),
+    "stretch_exponent": ("        else dz[k] = 10.0 * pow(4.0, (double)k / (double)(nz - 1));",
+                         "        else dz[k] = 10.0 * pow(4.0, (double)k / (double)nz);"),
+    "dzn_offset": ("    for (int k = 0; k < nz; k++) dzn[k] = (k < nz - 1) ? zn[k + 1] - zn[k] : 0.0;",
+                   "    for (int k = 0; k < nz; k++) dzn[k] = (k < nz - 1) ? zf[k + 1] - zf[k] : 0.0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "pw_oracle.c")).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, name
+    mpath = tmp_path / "mut.c"
+    mpath.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O1", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so), str(mpath), "-lm"],
+                   check=True)
+    caught = []
+    with oracle.use_library(str(so)):
+        for pin in PINS:
+            try:
+                pin()
+            except AssertionError:
+                caught.append(pin.__name__)
+    assert caught, f"planted mistake {name} passed every pin"
