@@ -1,0 +1,265 @@
+/*
+ * pwadv.h -- C-ABI of a single-GPU (sm_103a) library that computes the
+ * Piacsek-Williams (PW) advection source terms su, sv, sw of the wind fields
+ * u, v, w of a large-eddy model: the computation the paper (a directive-based
+ * hybrid of the Met Office NERC Cloud model) offloads to the GPU while the rest
+ * of the dynamics runs on the CPU (sections 2.1 and 3; the scheme is the energy
+ * conserving PW form named in section 3.1).
+ *
+ * Grid.  Arakawa C-grid, periodic in x and y, nx * ny columns of nz levels:
+ *   u(i,j,k) at (x_{i+1/2}, y_j, zn_k), v(i,j,k) at (x_i, y_{j+1/2}, zn_k),
+ *   w(i,j,k) at (x_i, y_j, zf_k), zf_k the top face of cell k.
+ * w at the ground face (below k = 0) is 0, and the lid face w(.,.,nz-1) is 0 by
+ * definition: the value stored there is never read and sw(.,.,nz-1) = 0.
+ *
+ * Field layout.  Every field and source buffer holds (nx+4) * (ny+4) * nzp
+ * elements: index ((i+2) * (ny+4) + (j+2)) * nzp + k for i in [-2, nx+2),
+ * j in [-2, ny+2), k in [0, nzp); k is contiguous, x/y halos are 2 wide,
+ * nzp >= nz is the padded column length given by pw_mesh_layout().  The library
+ * never reads padding k >= nz.  Base pointers must be 16-byte aligned.
+ *
+ * Memory and streams.  Every pointer argument named a field or a source is a
+ * DEVICE pointer owned by the caller.  The library owns meshes (coefficients,
+ * status word, reduction scratch) and batches.  Unless stated otherwise a call
+ * only enqueues work on `stream` (a cudaStream_t, NULL for the legacy default
+ * stream) and returns without synchronising; errors found by argument checks are
+ * returned at once, errors of the launch itself as PW_ERR_CUDA.
+ *
+ * Errors.  Every call returns a pw_status; pw_last_error() gives a thread-local
+ * text for the last failing call of the calling thread.
+ */
+#ifndef PWADV_H
+#define PWADV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PWADV_VERSION 1
+/* Largest nz a mesh may have (columns are processed in k chunks above ~240). */
+#define PW_MAX_NZ 4096
+
+typedef enum {
+    PW_OK = 0,
+    PW_ERR_ARG = -1,      /* null pointer or value out of range */
+    PW_ERR_SHAPE = -2,    /* sizes inconsistent with the mesh or beyond limits */
+    PW_ERR_ALIGN = -3,    /* a buffer is not 16-byte aligned */
+    PW_ERR_DTYPE = -4,    /* operation not available for the mesh dtype */
+    PW_ERR_LID = -5,      /* pw_check_lid found a non-zero lid value */
+    PW_ERR_CUDA = -6,     /* a CUDA runtime call failed (text in pw_last_error) */
+    PW_ERR_TIMEOUT = -7,  /* a kernel gave up waiting for an asynchronous copy */
+    PW_ERR_NOMEM = -8,    /* host or device allocation failed */
+    PW_ERR_IO = -9        /* the autotune cache file could not be read or written */
+} pw_status;
+
+/* Storage type of the fields and sources of a mesh. */
+typedef enum {
+    PW_F64 = 0,   /* u, v, w and su, sv, sw in binary64; result within 1e-12 of FP64 */
+    PW_F32 = 1,   /* binary32 storage and FP32 arithmetic */
+    PW_BF16 = 2   /* u, v, w in bfloat16; FP32 arithmetic; su, sv, sw in binary32 */
+} pw_dtype;
+
+/* Arithmetic used for PW_F64 meshes (ignored for the other dtypes). */
+typedef enum {
+    PW_ALGO_AUTO = 0,       /* PW_ALGO_F64_SPLIT */
+    PW_ALGO_F64_NATIVE = 1, /* FP64 instructions (the DP units of B300 are slow) */
+    PW_ALGO_F64_SPLIT = 2   /* each double split exactly into two floats; products
+                               by FMA-exact FP32 transforms; meets 1e-12 relative */
+} pw_algo;
+
+typedef struct {
+    int nx, ny, nz;          /* interior points: nx, ny >= 1; 1 <= nz <= PW_MAX_NZ */
+    double dx, dy;           /* horizontal spacing in m, > 0 */
+    const double *dz;        /* HOST array of nz layer thicknesses (m), or NULL for
+                                the geometric stretch dz(k) = 10 * 4^(k/(nz-1)) */
+    const double *rho_n;     /* HOST, nz reference densities at cell centres, or NULL */
+    const double *rho_w;     /* HOST, nz densities at the top faces, or NULL */
+    double rho0, H_rho;      /* rho = rho0 exp(-z/H_rho) where not given; both 0 means
+                                1.2 kg/m^3 and 8000 m; rho0 is also the ground density */
+    pw_dtype dtype;
+    pw_algo algo;
+} pw_mesh_desc;
+
+typedef struct pw_mesh pw_mesh;
+typedef struct pw_batch pw_batch;
+
+/* ---------------------------------------------------------------------------
+ * Mesh: grid, coefficients and layout (the constants the paper copies to the
+ * device once, at initialisation; section 3).
+ * -------------------------------------------------------------------------*/
+
+/* Create a mesh on the current CUDA device.  Computes, in FP64 on the GPU,
+ *   zf(k) = sum_{m<=k} dz(m), zn(k) = zf(k) - dz(k)/2, dzn(k) = zn(k+1) - zn(k),
+ *   rho_n, rho_w (given or rho0 exp(-z/H)), rho_w(-1) = rho0,
+ *   tzc1(k) = 0.25 rho_w(k-1) / (rho_n(k) dz(k)),
+ *   tzc2(k) = 0.25 rho_w(k)   / (rho_n(k) dz(k)),
+ *   tzd1(k) = 0.25 rho_n(k)   / (rho_w(k) dzn(k)),   k < nz-1 (else 0),
+ *   tzd2(k) = 0.25 rho_n(k+1) / (rho_w(k) dzn(k)),   k < nz-1 (else 0),
+ *   tcx = 0.25/dx, tcy = 0.25/dy,
+ * and FP32 copies of the vertical coefficients for the FP32/BF16 kernels.
+ * Synchronises `stream`.  On success *out owns device memory; free it with
+ * pw_mesh_destroy.  Returns PW_ERR_ARG / PW_ERR_SHAPE for bad descriptors. */
+pw_status pw_mesh_create(const pw_mesh_desc *desc, void *stream, pw_mesh **out);
+
+/* Free a mesh (NULL is allowed).  The caller must ensure no launch using it is
+ * still running. */
+void pw_mesh_destroy(pw_mesh *mesh);
+
+/* Layout of every field/source buffer of this mesh, in ELEMENTS: nzp (padded
+ * column length, a multiple of 8), stride_j = nzp, stride_i = (ny+4)*nzp, and
+ * the total count (nx+4)*(ny+4)*nzp.  Any output pointer may be NULL. */
+pw_status pw_mesh_layout(const pw_mesh *mesh, int64_t *nzp, int64_t *stride_j,
+                         int64_t *stride_i, int64_t *total);
+
+/* Copy the FP64 vertical grid to host memory `out` (12*nz doubles, in order
+ * dz, zf, zn, dzn, rho_n, rho_w, tzc1, tzc2, tzd1, tzd2, W_uv, W_w where
+ * W_uv = rho_n dz and W_w = rho_w dzn (0 on the lid face) are the energy
+ * weights) and tcx, tcy into out_h[2] (may be NULL).  Synchronous. */
+pw_status pw_mesh_coefficients(const pw_mesh *mesh, double *out, double *out_h);
+
+/* Read (and with clear != 0 reset) the mesh's device status word: 0, or
+ * PW_ERR_TIMEOUT when a kernel gave up waiting on an asynchronous copy since the
+ * last clear.  Synchronises `stream`. */
+pw_status pw_mesh_device_status(const pw_mesh *mesh, int clear, void *stream, int *status);
+
+/* Tile configuration used by the stencil launches of this mesh: rows of columns
+ * per CTA (tile_j, 1..32), columns marched per CTA along x (tile_i, >= 1).
+ * Set by pw_autotune or by hand; not safe while launches are being enqueued
+ * from another thread. */
+pw_status pw_mesh_set_tile(pw_mesh *mesh, int tile_j, int tile_i);
+pw_status pw_mesh_get_tile(const pw_mesh *mesh, int *tile_j, int *tile_i);
+
+/* ---------------------------------------------------------------------------
+ * Stencil entry points.
+ * -------------------------------------------------------------------------*/
+
+/* Periodic halo fill (the paper's halo swap at the start of a timestep,
+ * section 2.1, on one device): copies interior columns into the 2-wide x and y
+ * halos (corners included) of up to three fields of the mesh dtype, in place.
+ * f1 must be non-NULL; f2, f3 may be NULL. */
+pw_status pw_halo_periodic(const pw_mesh *mesh, void *f1, void *f2, void *f3, void *stream);
+
+/* PW advection source terms (section 3.1): with halos of u, v, w filled,
+ *  su = tcx [u(i-1)(u(i-1)+u(i)) - u(i+1)(u(i)+u(i+1))]
+ *     + tcy [u(j-1)(v(i,j-1)+v(i+1,j-1)) - u(j+1)(v(i,j)+v(i+1,j))]
+ *     + tzc1(k) u(k-1)(w(i,k-1)+w(i+1,k-1)) - tzc2(k) u(k+1)(w(i,k)+w(i+1,k))
+ *  sv = tcx [v(i-1)(u(i-1,j)+u(i-1,j+1)) - v(i+1)(u(i,j)+u(i,j+1))]
+ *     + tcy [v(j-1)(v(j-1)+v(j)) - v(j+1)(v(j)+v(j+1))]
+ *     + tzc1(k) v(k-1)(w(j,k-1)+w(j+1,k-1)) - tzc2(k) v(k+1)(w(j,k)+w(j+1,k))
+ *  sw = tcx [w(i-1)(u(i-1,k)+u(i-1,k+1)) - w(i+1)(u(i,k)+u(i,k+1))]
+ *     + tcy [w(j-1)(v(j-1,k)+v(j-1,k+1)) - w(j+1)(v(j,k)+v(j,k+1))]
+ *     + tzd1(k) w(k-1)(w(k-1)+w(k)) - tzd2(k) w(k+1)(w(k)+w(k+1)),  sw(nz-1) = 0,
+ * terms whose face lies on the ground or the lid being 0.  Unlisted indices are
+ * (i,j,k).  beta = 0 overwrites su, sv, sw; beta = 1 adds to them (dynamics
+ * components add into shared source terms, section 3).  Only interior points
+ * k < nz are written.  u, v, w are mesh dtype; su, sv, sw are binary64 for
+ * PW_F64 and binary32 otherwise.  Inputs and outputs must not overlap. */
+pw_status pw_advect(const pw_mesh *mesh, const void *u, const void *v, const void *w,
+                    void *su, void *sv, void *sw, int beta, void *stream);
+
+/* Adjoint (transpose of the Jacobian of the map (u,v,w) -> (su,sv,sw) at the
+ * given u, v, w) applied to incoming gradients gsu, gsv, gsw, with the periodic
+ * halo fold included: gu, gv, gw receive gradients with respect to the INTERIOR
+ * values (what the forward reads through a halo copy is added to the interior
+ * point it copies):
+ *   g = alpha * J(u,v,w)^T (gsu, gsv, gsw)            (beta = 0)
+ *   g = g + alpha * J(u,v,w)^T (gsu, gsv, gsw)        (beta = 1)
+ * Halos of u, v, w must be filled; the interior of gsu, gsv, gsw is read and
+ * THEIR HALO COLUMNS ARE OVERWRITTEN with periodic copies.  gw(.,.,nz-1) = 0
+ * (the lid is not a degree of freedom).  Only interior points k < nz of
+ * gu, gv, gw are written.  FP32 and FP64 meshes (FP64 in native FP64
+ * arithmetic); PW_ERR_DTYPE for BF16.  No argument may alias an output. */
+pw_status pw_advect_adjoint(const pw_mesh *mesh, const void *u, const void *v, const void *w,
+                            void *gsu, void *gsv, void *gsw,
+                            void *gu, void *gv, void *gw, double alpha, int beta, void *stream);
+
+/* Adjoint of one forward-Euler step x' = x + dt S(x) at the state x = (u,v,w):
+ *   g_out = g_in + dt * J(u,v,w)^T g_in,
+ * with the same halo conventions as pw_advect_adjoint (the halos of g_in are
+ * overwritten; g_out(w lid) = 0).  Used for reverse sweeps over Euler loops. */
+pw_status pw_euler_adjoint(const pw_mesh *mesh, const void *u, const void *v, const void *w,
+                           void *gu_in, void *gv_in, void *gw_in,
+                           void *gu_out, void *gv_out, void *gw_out, double dt, void *stream);
+
+/* Forward-Euler step of the prognostic fields (the "step fields" integration of
+ * section 3, advection-only): x <- x + dt * s for x in (u, v, w), s in
+ * (su, sv, sw) on interior points k < nz, and the periodic halos of u, v, w are
+ * refreshed in the same pass.  FP32 and FP64 meshes. */
+pw_status pw_euler(const pw_mesh *mesh, void *u, void *v, void *w,
+                   const void *su, const void *sv, const void *sw, double dt, void *stream);
+
+/* Conservation diagnostics, accumulated in FP64 on the GPU with a deterministic
+ * two-pass tree reduction (the order does not depend on timing).  With weights
+ * W = rho_n dz on u/v levels and rho_w dzn on w faces (lid face 0), for each
+ * component c in (u, v, w) with source S:
+ *   out[4c+0] = sum W phi S,   out[4c+1] = sum W |phi S|,
+ *   out[4c+2] = sum W S,       out[4c+3] = sum W |S|,
+ * so the energy residual is R_E = out[4c]/out[4c+1] (0 up to rounding for any
+ * fields: the PW form conserves energy) and R_M = out[4c+2]/out[4c+3].
+ * out is a HOST array of 12 doubles.  Synchronises `stream`.  Uses scratch that
+ * the mesh owns, so concurrent calls on one mesh race. */
+pw_status pw_residuals(const pw_mesh *mesh, const void *u, const void *v, const void *w,
+                       const void *su, const void *sv, const void *sw, double *out,
+                       void *stream);
+
+/* Return PW_ERR_LID if any lid value w(i,j,nz-1) (interior) is not 0, else
+ * PW_OK.  Synchronises `stream`. */
+pw_status pw_check_lid(const pw_mesh *mesh, const void *w, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched ensembles: many independent subdomains (uneven sizes, own dx and dz)
+ * advected in ONE persistent launch.
+ * -------------------------------------------------------------------------*/
+
+/* Create a batch over n meshes (all PW_F32, or all PW_F64 / PW_BF16); the
+ * meshes must outlive the batch.  Device tables are built on `stream` and the
+ * call synchronises it. */
+pw_status pw_batch_create(pw_mesh *const *meshes, int n, void *stream, pw_batch **out);
+void pw_batch_destroy(pw_batch *batch);
+
+/* Bind member field buffers: host arrays of n device pointers each.  Copies the
+ * member descriptors to the device and synchronises `stream`; after this,
+ * pw_advect_batched enqueues a single kernel with no host-to-device copy and can
+ * be captured in a CUDA graph.  Halos of every member must be filled before an
+ * advect. */
+pw_status pw_batch_set_fields(pw_batch *batch, void *const *u, void *const *v, void *const *w,
+                              void *const *su, void *const *sv, void *const *sw, void *stream);
+
+/* su, sv, sw of every member (same formulas as pw_advect) in one launch.  CTAs
+ * pull tiles from a device work counter that this call resets on `stream`. */
+pw_status pw_advect_batched(pw_batch *batch, int beta, void *stream);
+
+/* Periodic halo fill of the bound u, v, w of every member in one launch. */
+pw_status pw_batch_halo(pw_batch *batch, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Tile autotuner (tile shapes chosen by timing candidates on the device).
+ * -------------------------------------------------------------------------*/
+
+/* Time each candidate tile (tile_j, tile_i) with pw_advect on the given buffers
+ * (their contents are overwritten in su, sv, sw only), keep the fastest in the
+ * mesh, and, if cache_path is not NULL, record it in a text cache keyed by
+ * (nx, ny, nz, dtype, algo, SM count) -- a later call with the same key reads
+ * the cache instead of timing.  Synchronises `stream`. */
+pw_status pw_autotune(pw_mesh *mesh, const void *u, const void *v, const void *w,
+                      void *su, void *sv, void *sw, const char *cache_path, void *stream,
+                      float *best_ms);
+
+/* Same for a batch whose fields are bound: picks one tile shape per size class
+ * of members (by nz) and the persistent grid size. */
+pw_status pw_batch_autotune(pw_batch *batch, const char *cache_path, void *stream, float *best_ms);
+
+/* ---------------------------------------------------------------------------
+ * Errors and version.
+ * -------------------------------------------------------------------------*/
+const char *pw_status_string(pw_status status);
+const char *pw_last_error(void);
+int pw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PWADV_H */

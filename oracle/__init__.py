@@ -39,6 +39,8 @@ def lib():
         L.pwo_adjoint.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_D] * 4 + [_D] * 3
                                   + [_D] * 3 + [_D] * 3 + [ctypes.c_int])
         L.pwo_adjoint.restype = None
+        L.pwo_adjoint_mode.argtypes = L.pwo_adjoint.argtypes + [ctypes.c_int]
+        L.pwo_adjoint_mode.restype = None
         L.pwo_residual_sums.argtypes = [ctypes.c_int] * 3 + [_D] * 4 + [_D] * 6 + [_D]
         L.pwo_residual_sums.restype = None
         L.pwo_face_divergence.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 2 + [_D] * 4 + [_D] * 3 + [_D]
@@ -160,6 +162,17 @@ def adjoint(c: Coeffs, u, v, w, gsu, gsv, gsw):
     g = [np.zeros_like(u) for _ in range(3)]
     lib().pwo_adjoint(nx, ny, nz, *c.args(), _p(u), _p(v), _p(w), _p(gsu), _p(gsv), _p(gsw),
                       *[_p(x) for x in g], 0)
+    return tuple(g)
+
+
+def adjoint_cond(c: Coeffs, u, v, w, gsu, gsv, gsw):
+    """Per-point sums of |contribution| of the gradient (its condition sums)."""
+    u, v, w = _f64(u), _f64(v), _f64(w)
+    gsu, gsv, gsw = _f64(gsu), _f64(gsv), _f64(gsw)
+    nx, ny, nz = _shape(u)
+    g = [np.zeros_like(u) for _ in range(3)]
+    lib().pwo_adjoint_mode(nx, ny, nz, *c.args(), _p(u), _p(v), _p(w), _p(gsu), _p(gsv), _p(gsw),
+                           *[_p(x) for x in g], 0, 1)
     return tuple(g)
 
 

@@ -329,6 +329,12 @@ static size_t pidx(const pwo_grid *g, long i, long j, long k)
     return ((size_t)wrap(i, g->nx) * (size_t)g->ny + (size_t)wrap(j, g->ny)) * (size_t)g->nz + (size_t)k;
 }
 
+void pwo_adjoint_mode(int nx, int ny, int nz, double tcx, double tcy,
+                      const double *tzc1, const double *tzc2, const double *tzd1, const double *tzd2,
+                      const double *u, const double *v, const double *w,
+                      const double *gsu, const double *gsv, const double *gsw,
+                      double *gu, double *gv, double *gw, int beta, int abs_mode);
+
 /*
  * gu, gv, gw = J(u,v,w)^T (gsu, gsv, gsw).  If beta is 0 the outputs are
  * overwritten, otherwise added to.  Sequential (scatter) so the summation order
@@ -339,6 +345,19 @@ void pwo_adjoint(int nx, int ny, int nz, double tcx, double tcy,
                  const double *u, const double *v, const double *w,
                  const double *gsu, const double *gsv, const double *gsw,
                  double *gu, double *gv, double *gw, int beta)
+{
+    pwo_adjoint_mode(nx, ny, nz, tcx, tcy, tzc1, tzc2, tzd1, tzd2, u, v, w, gsu, gsv, gsw,
+                     gu, gv, gw, beta, 0);
+}
+
+/* Same scatter with every contribution replaced by its absolute value
+ * (abs_mode = 1): the per-point condition sums of the gradient, used to scale
+ * tolerances of reduced-precision gradients. */
+void pwo_adjoint_mode(int nx, int ny, int nz, double tcx, double tcy,
+                      const double *tzc1, const double *tzc2, const double *tzd1, const double *tzd2,
+                      const double *u, const double *v, const double *w,
+                      const double *gsu, const double *gsv, const double *gsw,
+                      double *gu, double *gv, double *gw, int beta, int abs_mode)
 {
     pwo_grid g;
     fill_grid(&g, nx, ny, nz, tcx, tcy, tzc1, tzc2, tzd1, tzd2);
@@ -370,6 +389,12 @@ void pwo_adjoint(int nx, int ny, int nz, double tcx, double tcy,
                     const double *a = fld[T->a];
                     double phi = fld[T->src][P];
                     double sc = T->sign * coef * y;
+                    if (abs_mode) {
+                        gs[T->src][P] += fabs(sc) * (fabs(a[Q1]) + fabs(a[Q2]));
+                        gs[T->a][Q1] += fabs(sc * phi);
+                        gs[T->a][Q2] += fabs(sc * phi);
+                        continue;
+                    }
                     gs[T->src][P] += sc * (a[Q1] + a[Q2]);
                     gs[T->a][Q1] += sc * phi;
                     gs[T->a][Q2] += sc * phi;

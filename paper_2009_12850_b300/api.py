@@ -1,0 +1,179 @@
+"""Torch-facing wrapper of the C-ABI: a Mesh owns a pw_mesh and allocates,
+validates and passes device tensors.  PyTorch only provides device memory and
+the current stream; all arithmetic happens in libpwadv.so.
+
+Field tensors have the library layout: shape (nx+4, ny+4, nzp), contiguous,
+k fastest, 2-wide periodic halos in x and y.  ``Mesh.interior(t)`` is the
+(nx, ny, nz) view of the interior.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DT = {"f64": L.PW_F64, "f32": L.PW_F32, "bf16": L.PW_BF16}
+_ALGO = {"auto": L.PW_ALGO_AUTO, "native": L.PW_ALGO_F64_NATIVE, "split": L.PW_ALGO_F64_SPLIT}
+_TORCH_IN = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+_TORCH_OUT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.float32}
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host(a):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Mesh:
+    def __init__(self, nx, ny, nz, dx, dy=None, dz=None, rho_n=None, rho_w=None, rho0=0.0, H=0.0,
+                 dtype="f64", algo="auto", device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2009_12850_b300 needs a CUDA device")
+        self.device = torch.device(device or "cuda")
+        self.dtype = dtype
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dx = float(dx)
+        self.dy = float(dx if dy is None else dy)
+        self._keep = [_host(dz), _host(rho_n), _host(rho_w)]
+        d = L.pw_mesh_desc()
+        d.nx, d.ny, d.nz, d.dx, d.dy = self.nx, self.ny, self.nz, self.dx, self.dy
+        d.dz, d.rho_n, d.rho_w = (k[1] for k in self._keep)
+        d.rho0, d.H_rho = float(rho0), float(H)
+        d.dtype, d.algo = _DT[dtype], _ALGO[algo]
+        with torch.cuda.device(self.device):
+            self.handle = L.pw_mesh_create(d, _stream())
+        self.nzp, self.stride_j, self.stride_i, self.total = L.pw_mesh_layout(self.handle)
+        self.in_dtype = _TORCH_IN[dtype]
+        self.out_dtype = _TORCH_OUT[dtype]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.pw_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ layout
+    @property
+    def shape(self):
+        return (self.nx + 4, self.ny + 4, self.nzp)
+
+    def empty(self, dtype=None):
+        return torch.empty(self.shape, dtype=dtype or self.in_dtype, device=self.device)
+
+    def zeros(self, dtype=None):
+        return torch.zeros(self.shape, dtype=dtype or self.in_dtype, device=self.device)
+
+    def empty_out(self):
+        return self.empty(self.out_dtype)
+
+    def interior(self, t):
+        return t[2:self.nx + 2, 2:self.ny + 2, :self.nz]
+
+    def from_interior(self, arr, dtype=None, fill_halo=True):
+        """Field tensor from an (nx, ny, nz) array: interior copied, padding 0,
+        halos filled on the device by the library."""
+        t = self.zeros(dtype)
+        src = torch.as_tensor(np.ascontiguousarray(arr)) if isinstance(arr, np.ndarray) else arr
+        self.interior(t).copy_(src.to(device=self.device, dtype=t.dtype))
+        if fill_halo:
+            self.halo(t)
+        return t
+
+    def _check(self, t, name, out=False):
+        want = self.out_dtype if out else self.in_dtype
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != want:
+            raise TypeError(f"{name} must be {want}, got {t.dtype}")
+        if t.numel() != self.total or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with {self.total} elements (shape {self.shape})")
+        return ctypes.c_void_p(t.data_ptr())
+
+    # ------------------------------------------------------------------ calls
+    def coefficients(self):
+        vals, (tcx, tcy) = L.pw_mesh_coefficients(self.handle, self.nz)
+        a = np.array(vals).reshape(12, self.nz)
+        names = ["dz", "zf", "zn", "dzn", "rho_n", "rho_w", "tzc1", "tzc2", "tzd1", "tzd2", "W_uv", "W_w"]
+        out = {n: a[q] for q, n in enumerate(names)}
+        out["tcx"], out["tcy"] = tcx, tcy
+        return out
+
+    def halo(self, f1, f2=None, f3=None, stream=None):
+        ps = [self._check(f1, "f1")] + [self._check(f, "f") if f is not None else None for f in (f2, f3)]
+        L.pw_halo_periodic(self.handle, ps[0], ps[1], ps[2], _stream(stream))
+
+    def advect(self, u, v, w, su=None, sv=None, sw=None, beta=0, stream=None):
+        su = self.empty_out() if su is None else su
+        sv = self.empty_out() if sv is None else sv
+        sw = self.empty_out() if sw is None else sw
+        L.pw_advect(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                    self._check(su, "su", True), self._check(sv, "sv", True), self._check(sw, "sw", True),
+                    beta, _stream(stream))
+        return su, sv, sw
+
+    def adjoint(self, u, v, w, gsu, gsv, gsw, gu=None, gv=None, gw=None, alpha=1.0, beta=0, stream=None):
+        gu = self.zeros() if gu is None else gu
+        gv = self.zeros() if gv is None else gv
+        gw = self.zeros() if gw is None else gw
+        L.pw_advect_adjoint(self.handle, *(self._check(t, n) for t, n in ((u, "u"), (v, "v"), (w, "w"))),
+                            *(self._check(t, n) for t, n in ((gsu, "gsu"), (gsv, "gsv"), (gsw, "gsw"))),
+                            *(self._check(t, n) for t, n in ((gu, "gu"), (gv, "gv"), (gw, "gw"))),
+                            alpha, beta, _stream(stream))
+        return gu, gv, gw
+
+    def euler_adjoint(self, u, v, w, gu_in, gv_in, gw_in, gu_out=None, gv_out=None, gw_out=None, dt=1.0,
+                      stream=None):
+        gu_out = self.zeros() if gu_out is None else gu_out
+        gv_out = self.zeros() if gv_out is None else gv_out
+        gw_out = self.zeros() if gw_out is None else gw_out
+        L.pw_euler_adjoint(self.handle, *(self._check(t, "x") for t in (u, v, w)),
+                           *(self._check(t, "g_in") for t in (gu_in, gv_in, gw_in)),
+                           *(self._check(t, "g_out") for t in (gu_out, gv_out, gw_out)), dt, _stream(stream))
+        return gu_out, gv_out, gw_out
+
+    def euler(self, u, v, w, su, sv, sw, dt, stream=None):
+        L.pw_euler(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                   self._check(su, "su", True), self._check(sv, "sv", True), self._check(sw, "sw", True),
+                   dt, _stream(stream))
+
+    def residual_sums(self, u, v, w, su, sv, sw, stream=None):
+        out = L.pw_residuals(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                             self._check(su, "su", True), self._check(sv, "sv", True),
+                             self._check(sw, "sw", True), _stream(stream))
+        return np.array(out).reshape(3, 4)
+
+    def residuals(self, u, v, w, su, sv, sw, stream=None):
+        s = self.residual_sums(u, v, w, su, sv, sw, stream)
+        re = tuple(s[q, 0] / s[q, 1] if s[q, 1] else 0.0 for q in range(3))
+        rm = tuple(s[q, 2] / s[q, 3] if s[q, 3] else 0.0 for q in range(3))
+        return re, rm
+
+    def check_lid(self, w, stream=None):
+        return L.pw_check_lid(self.handle, self._check(w, "w"), _stream(stream)) == L.PW_OK
+
+    def device_status(self, clear=True, stream=None):
+        return L.pw_mesh_device_status(self.handle, clear, _stream(stream))
+
+    def set_tile(self, tile_j, tile_i):
+        L.pw_mesh_set_tile(self.handle, tile_j, tile_i)
+
+    def get_tile(self):
+        return L.pw_mesh_get_tile(self.handle)
+
+    def autotune(self, u, v, w, su, sv, sw, cache_path=None, stream=None):
+        return L.pw_autotune(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                             self._check(su, "su", True), self._check(sv, "sv", True),
+                             self._check(sw, "sw", True), cache_path, _stream(stream))

@@ -1,0 +1,171 @@
+// pw_internal.h -- shared host/device definitions of the PW advection library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pwadv.h"
+
+// ---------------------------------------------------------------------------
+// host-side objects
+// ---------------------------------------------------------------------------
+struct pw_mesh {
+    int nx, ny, nz;
+    int nzp;                 // padded column length (elements), multiple of 8
+    int64_t sj, si, total;   // strides / total count in elements
+    double dx, dy, tcx, tcy;
+    pw_dtype dtype;
+    pw_algo algo;
+    int device;
+    int num_sms;
+    double *coef64;          // device, 12*nz: dz zf zn dzn rho_n rho_w tzc1 tzc2 tzd1 tzd2 Wuv Ww
+    float *coef32;           // device, 4*nz: tzc1 tzc2 tzd1 tzd2
+    double *partials;        // device, residual scratch: (PW_RED_BLOCKS + 1) * 12 doubles
+    int *status;             // device: [0] timeout status (0 or PW_ERR_TIMEOUT), [1] lid flag
+    int tile_j, tile_i;      // stencil tile: rows per CTA, columns marched per CTA
+};
+
+// one member of a batch as the persistent kernel sees it
+struct PwMember {
+    const void *u, *v, *w;
+    void *su, *sv, *sw;
+    const float *coef;       // tzc1 tzc2 tzd1 tzd2, 4*nz
+    int nx, ny, nz, nzp;
+    float tcx, tcy;
+    int tile_j, tile_i;      // tile shape for this member
+    int tiles_j, tiles_i;    // tile counts
+    int first_tile;          // prefix sum over members
+    int pad_;
+};
+
+struct pw_batch {
+    int n;
+    pw_mesh **meshes;
+    PwMember *host_members;
+    PwMember *dev_members;
+    int *counter;            // device work counter
+    int *status;
+    int total_tiles;
+    int grid;                // persistent CTAs
+    int max_threads;         // largest CTA any member needs
+    size_t smem;             // dynamic shared memory of the launch
+    int bound;               // fields bound
+    pw_dtype dtype;
+};
+
+// reduction geometry of pw_residuals (fixed so the order of sums is fixed)
+#define PW_RED_BLOCKS 592
+#define PW_RED_THREADS 256
+
+// bounded waits: ~1 s at 2 GHz for a copy the kernel needs; ~50 ms when a
+// kernel that already gave up drains copies still in flight.  On expiry the
+// kernel records PW_ERR_TIMEOUT in the mesh status word, which is sticky: CTAs
+// that start after it is set return at once, until the host clears it.
+#define PW_WAIT_CYCLES (2000000000LL)
+#define PW_DRAIN_CYCLES (100000000LL)
+
+// error helpers (pw_mesh.cu)
+pw_status pw_fail(pw_status st, const char *fmt, ...);
+pw_status pw_cuda_fail(cudaError_t e, const char *what);
+#define PW_CUDA(call)                                               \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return pw_cuda_fail(e_, #call);      \
+    } while (0)
+
+int pw_elem_in(pw_dtype d);    // bytes per field element
+int pw_elem_out(pw_dtype d);   // bytes per source element
+pw_status pw_check_ptr(const void *p, const char *name);
+
+// TMA descriptor for one field of a mesh: box {kbox, rows, 1} over
+// dims {nzp, ny+4, nx+4}.
+pw_status pw_make_field_map(CUtensorMap *map, const void *base, pw_dtype dtype, int nx, int ny,
+                            int nzp, int kbox, int rows);
+
+// launchers (pw_advect.cu / pw_adjoint.cu)
+pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const void *w,
+                           void *su, void *sv, void *sw, int beta, cudaStream_t st,
+                           int tile_j, int tile_i);
+pw_status pw_launch_halo(const pw_mesh *m, void *const *f, int nf, cudaStream_t st);
+pw_status pw_launch_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
+                              const void *su, const void *sv, const void *sw, double *partials,
+                              double *dout, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t pw_smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void pw_mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(pw_smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void pw_fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void pw_mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(pw_smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool pw_mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(pw_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier with a cycle limit.  Returns false on
+// expiry (the caller records PW_ERR_TIMEOUT and leaves).
+__device__ __forceinline__ bool pw_mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                     long long limit = PW_WAIT_CYCLES) {
+    if (pw_mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!pw_mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
+// true when an earlier CTA (or launch) on this status word has timed out
+__device__ __forceinline__ bool pw_status_failed(const int *status) {
+    return *reinterpret_cast<const volatile int *>(status) != 0;
+}
+
+__device__ __forceinline__ void pw_tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                               int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(pw_smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(pw_smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void pw_prefetch_map(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// scalar conversions of the storage types to the compute type
+template <typename TC>
+__device__ __forceinline__ TC pw_to(double x) { return (TC)x; }
+template <typename TC>
+__device__ __forceinline__ TC pw_to(float x) { return (TC)x; }
+template <typename TC>
+__device__ __forceinline__ TC pw_to(__nv_bfloat16 x) { return (TC)__bfloat162float(x); }
+
+#endif  // __CUDACC__

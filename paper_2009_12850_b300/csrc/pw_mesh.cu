@@ -1,0 +1,592 @@
+// pw_mesh.cu -- mesh set-up, coefficients (FP64 on the GPU), periodic halo
+// fill, forward-Euler update with halo refresh, conservation reductions and
+// the error plumbing of the C-ABI.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "pw_internal.h"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_last_error[512] = "";
+
+pw_status pw_fail(pw_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+pw_status pw_cuda_fail(cudaError_t e, const char *what) {
+    return pw_fail(PW_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+extern "C" const char *pw_last_error(void) { return g_last_error; }
+
+extern "C" const char *pw_status_string(pw_status s) {
+    switch (s) {
+        case PW_OK: return "ok";
+        case PW_ERR_ARG: return "invalid argument";
+        case PW_ERR_SHAPE: return "shape mismatch or out of range";
+        case PW_ERR_ALIGN: return "buffer not 16-byte aligned";
+        case PW_ERR_DTYPE: return "operation not available for this dtype";
+        case PW_ERR_LID: return "non-zero lid value";
+        case PW_ERR_CUDA: return "CUDA error";
+        case PW_ERR_TIMEOUT: return "device wait timed out";
+        case PW_ERR_NOMEM: return "out of memory";
+        case PW_ERR_IO: return "autotune cache i/o error";
+    }
+    return "unknown status";
+}
+
+extern "C" int pw_version(void) { return PWADV_VERSION; }
+
+int pw_elem_in(pw_dtype d) { return d == PW_F64 ? 8 : d == PW_F32 ? 4 : 2; }
+int pw_elem_out(pw_dtype d) { return d == PW_F64 ? 8 : 4; }
+
+pw_status pw_check_ptr(const void *p, const char *name) {
+    if (!p) return pw_fail(PW_ERR_ARG, "%s is NULL", name);
+    if (((uintptr_t)p) & 15u) return pw_fail(PW_ERR_ALIGN, "%s is not 16-byte aligned", name);
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// TMA descriptors
+// ---------------------------------------------------------------------------
+typedef CUresult (*pw_encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                       const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                       const cuuint32_t *, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                       CUtensorMapFloatOOBfill);
+
+static pw_encode_tiled_fn pw_encoder() {
+    static pw_encode_tiled_fn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (pw_encode_tiled_fn)p;
+    }
+    return fn;
+}
+
+pw_status pw_make_field_map(CUtensorMap *map, const void *base, pw_dtype dtype, int nx, int ny,
+                            int nzp, int kbox, int rows) {
+    pw_encode_tiled_fn enc = pw_encoder();
+    if (!enc) return pw_fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    int es = pw_elem_in(dtype);
+    CUtensorMapDataType dt = dtype == PW_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                             : dtype == PW_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint64_t dims[3] = {(cuuint64_t)nzp, (cuuint64_t)(ny + 4), (cuuint64_t)(nx + 4)};
+    cuuint64_t strides[2] = {(cuuint64_t)nzp * es, (cuuint64_t)nzp * es * (ny + 4)};
+    cuuint32_t box[3] = {(cuuint32_t)kbox, (cuuint32_t)rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return pw_fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d): box %u x %u, nzp %d",
+                       (int)r, box[0], box[1], nzp);
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A1: vertical grid and coefficients in FP64 (one thread: nz is small and the
+// prefix sum is sequential)
+// ---------------------------------------------------------------------------
+__global__ void pw_coeffs_kernel(int nz, const double *dz_in, const double *rn_in,
+                                 const double *rw_in, int have_dz, int have_rn, int have_rw,
+                                 double rho0, double H, double *c64, float *c32) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double *dz = c64, *zf = c64 + nz, *zn = c64 + 2 * nz, *dzn = c64 + 3 * nz;
+    double *rn = c64 + 4 * nz, *rw = c64 + 5 * nz;
+    double *t1 = c64 + 6 * nz, *t2 = c64 + 7 * nz, *d1 = c64 + 8 * nz, *d2 = c64 + 9 * nz;
+    double *wuv = c64 + 10 * nz, *ww = c64 + 11 * nz;
+    for (int k = 0; k < nz; k++) {
+        if (have_dz) dz[k] = dz_in[k];
+        else if (nz == 1) dz[k] = 10.0;
+        else dz[k] = 10.0 * pow(4.0, (double)k / (double)(nz - 1));
+    }
+    double z = 0.0;
+    for (int k = 0; k < nz; k++) {
+        z += dz[k];
+        zf[k] = z;
+        zn[k] = z - 0.5 * dz[k];
+    }
+    for (int k = 0; k < nz; k++) dzn[k] = (k < nz - 1) ? zn[k + 1] - zn[k] : 0.0;
+    for (int k = 0; k < nz; k++) {
+        rn[k] = have_rn ? rn_in[k] : rho0 * exp(-zn[k] / H);
+        rw[k] = have_rw ? rw_in[k] : rho0 * exp(-zf[k] / H);
+    }
+    for (int k = 0; k < nz; k++) {
+        double below = (k == 0) ? rho0 : rw[k - 1];
+        t1[k] = 0.25 * below / (rn[k] * dz[k]);
+        t2[k] = 0.25 * rw[k] / (rn[k] * dz[k]);
+        if (k < nz - 1) {
+            d1[k] = 0.25 * rn[k] / (rw[k] * dzn[k]);
+            d2[k] = 0.25 * rn[k + 1] / (rw[k] * dzn[k]);
+        } else {
+            d1[k] = 0.0;
+            d2[k] = 0.0;
+        }
+        wuv[k] = rn[k] * dz[k];
+        ww[k] = (k < nz - 1) ? rw[k] * dzn[k] : 0.0;
+        c32[k] = (float)t1[k];
+        c32[nz + k] = (float)t2[k];
+        c32[2 * nz + k] = (float)d1[k];
+        c32[3 * nz + k] = (float)d2[k];
+    }
+}
+
+static void pw_mesh_free(pw_mesh *m) {
+    if (!m) return;
+    cudaFree(m->coef64);
+    cudaFree(m->coef32);
+    cudaFree(m->partials);
+    cudaFree(m->status);
+    free(m);
+}
+
+extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh **out) {
+    if (!d || !out) return pw_fail(PW_ERR_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nz > PW_MAX_NZ)
+        return pw_fail(PW_ERR_SHAPE, "bad sizes nx=%d ny=%d nz=%d (need >= 1, nz <= %d)", d->nx,
+                       d->ny, d->nz, PW_MAX_NZ);
+    if ((int64_t)(d->nx + 4) * (d->ny + 4) > (int64_t)1 << 31 || d->nx > 1 << 20 || d->ny > 1 << 20)
+        return pw_fail(PW_ERR_SHAPE, "horizontal size too large");
+    if (!(d->dx > 0) || !(d->dy > 0)) return pw_fail(PW_ERR_ARG, "dx and dy must be > 0");
+    if (d->dtype != PW_F64 && d->dtype != PW_F32 && d->dtype != PW_BF16)
+        return pw_fail(PW_ERR_DTYPE, "unknown dtype %d", (int)d->dtype);
+    if (d->algo < PW_ALGO_AUTO || d->algo > PW_ALGO_F64_SPLIT)
+        return pw_fail(PW_ERR_ARG, "unknown algo %d", (int)d->algo);
+    double rho0 = d->rho0, H = d->H_rho;
+    if (rho0 == 0.0 && H == 0.0) {
+        rho0 = 1.2;
+        H = 8000.0;
+    }
+    if (!(rho0 > 0) || H == 0.0) return pw_fail(PW_ERR_ARG, "rho0 must be > 0 and H_rho != 0");
+    int nz = d->nz;
+    for (int k = 0; d->dz && k < nz; k++)
+        if (!(d->dz[k] > 0)) return pw_fail(PW_ERR_ARG, "dz[%d] must be > 0", k);
+    for (int k = 0; d->rho_n && k < nz; k++)
+        if (!(d->rho_n[k] > 0)) return pw_fail(PW_ERR_ARG, "rho_n[%d] must be > 0", k);
+    for (int k = 0; d->rho_w && k < nz; k++)
+        if (!(d->rho_w[k] > 0)) return pw_fail(PW_ERR_ARG, "rho_w[%d] must be > 0", k);
+
+    pw_mesh *m = (pw_mesh *)calloc(1, sizeof(pw_mesh));
+    if (!m) return pw_fail(PW_ERR_NOMEM, "host allocation");
+    m->nx = d->nx;
+    m->ny = d->ny;
+    m->nz = nz;
+    m->nzp = (nz + 7) / 8 * 8;
+    m->sj = m->nzp;
+    m->si = (int64_t)(d->ny + 4) * m->nzp;
+    m->total = (int64_t)(d->nx + 4) * m->si;
+    m->dx = d->dx;
+    m->dy = d->dy;
+    m->tcx = 0.25 / d->dx;
+    m->tcy = 0.25 / d->dy;
+    m->dtype = d->dtype;
+    m->algo = d->algo == PW_ALGO_AUTO ? PW_ALGO_F64_NATIVE : d->algo;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+    if (e != cudaSuccess) {
+        pw_mesh_free(m);
+        return pw_cuda_fail(e, "device query");
+    }
+    m->tile_j = d->dtype == PW_F64 ? 4 : 8;
+    m->tile_i = 32;
+    double *tmp = nullptr;
+    if ((e = cudaMalloc(&m->coef64, 12 * (size_t)nz * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&m->coef32, 4 * (size_t)nz * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&m->partials, (PW_RED_BLOCKS + 1) * 12 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&m->status, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&tmp, 3 * (size_t)nz * sizeof(double))) != cudaSuccess) {
+        pw_mesh_free(m);
+        cudaFree(tmp);
+        return pw_cuda_fail(e, "cudaMalloc (mesh)");
+    }
+    pw_status rs = PW_OK;
+    do {
+        if (d->dz && (e = cudaMemcpyAsync(tmp, d->dz, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if (d->rho_n && (e = cudaMemcpyAsync(tmp + nz, d->rho_n, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if (d->rho_w && (e = cudaMemcpyAsync(tmp + 2 * nz, d->rho_w, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(m->status, 0, 2 * sizeof(int), st)) != cudaSuccess) break;
+        pw_coeffs_kernel<<<1, 32, 0, st>>>(nz, tmp, tmp + nz, tmp + 2 * nz, d->dz != nullptr,
+                                           d->rho_n != nullptr, d->rho_w != nullptr, rho0, H,
+                                           m->coef64, m->coef32);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        pw_mesh_free(m);
+        return pw_cuda_fail(e, "mesh coefficient set-up");
+    }
+    // sanity: the coefficients must be finite
+    double *h = (double *)malloc(12 * (size_t)nz * sizeof(double));
+    if (!h) {
+        pw_mesh_free(m);
+        return pw_fail(PW_ERR_NOMEM, "host allocation");
+    }
+    e = cudaMemcpy(h, m->coef64, 12 * (size_t)nz * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rs = pw_cuda_fail(e, "coefficient read-back");
+    for (int q = 0; rs == PW_OK && q < 12 * nz; q++)
+        if (!isfinite(h[q])) rs = pw_fail(PW_ERR_ARG, "non-finite vertical coefficient (check dz/rho)");
+    free(h);
+    if (rs != PW_OK) {
+        pw_mesh_free(m);
+        return rs;
+    }
+    *out = m;
+    return PW_OK;
+}
+
+extern "C" void pw_mesh_destroy(pw_mesh *m) { pw_mesh_free(m); }
+
+extern "C" pw_status pw_mesh_layout(const pw_mesh *m, int64_t *nzp, int64_t *sj, int64_t *si,
+                                    int64_t *total) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    if (nzp) *nzp = m->nzp;
+    if (sj) *sj = m->sj;
+    if (si) *si = m->si;
+    if (total) *total = m->total;
+    return PW_OK;
+}
+
+extern "C" pw_status pw_mesh_coefficients(const pw_mesh *m, double *out, double *out_h) {
+    if (!m || !out) return pw_fail(PW_ERR_ARG, "mesh and out must not be NULL");
+    PW_CUDA(cudaMemcpy(out, m->coef64, 12 * (size_t)m->nz * sizeof(double), cudaMemcpyDeviceToHost));
+    if (out_h) {
+        out_h[0] = m->tcx;
+        out_h[1] = m->tcy;
+    }
+    return PW_OK;
+}
+
+extern "C" pw_status pw_mesh_device_status(const pw_mesh *m, int clear, void *stream, int *status) {
+    if (!m || !status) return pw_fail(PW_ERR_ARG, "mesh and status must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    PW_CUDA(cudaMemcpyAsync(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (clear) PW_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), st));
+    PW_CUDA(cudaStreamSynchronize(st));
+    *status = h;
+    return PW_OK;
+}
+
+extern "C" pw_status pw_mesh_set_tile(pw_mesh *m, int tile_j, int tile_i) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    if (tile_j < 1 || tile_j > 32 || tile_i < 1 || tile_i > 1 << 20)
+        return pw_fail(PW_ERR_ARG, "tile_j must be in 1..32 and tile_i >= 1");
+    m->tile_j = tile_j;
+    m->tile_i = tile_i;
+    return PW_OK;
+}
+
+extern "C" pw_status pw_mesh_get_tile(const pw_mesh *m, int *tile_j, int *tile_i) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    if (tile_j) *tile_j = m->tile_j;
+    if (tile_i) *tile_i = m->tile_i;
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A2: periodic halo fill.  One warp per halo column; each lane copies 16-byte
+// chunks of the column from its periodic image in the interior.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pw_wrap(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+__global__ void pw_halo_kernel(char *f0, char *f1, char *f2, int nx, int ny, int64_t col_bytes,
+                               int64_t col_stride, int nchunk) {
+    char *f = blockIdx.y == 0 ? f0 : blockIdx.y == 1 ? f1 : f2;
+    int warps = blockDim.x >> 5;
+    int64_t c = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    int64_t rows = 4LL * (ny + 4);      // full halo rows ih in {0,1,nx+2,nx+3}
+    int64_t total = rows + 4LL * nx;    // plus side halos jh in {0,1,ny+2,ny+3}
+    if (c >= total) return;
+    int ih, jh;
+    if (c < rows) {
+        int r = (int)(c / (ny + 4));
+        ih = r < 2 ? r : nx + r;
+        jh = (int)(c % (ny + 4));
+    } else {
+        int64_t q = c - rows;
+        ih = 2 + (int)(q / 4);
+        int s = (int)(q % 4);
+        jh = s < 2 ? s : ny + s;
+    }
+    int is = pw_wrap(ih - 2, nx) + 2, js = pw_wrap(jh - 2, ny) + 2;
+    const int4 *src = reinterpret_cast<const int4 *>(f + ((int64_t)is * (ny + 4) + js) * col_stride);
+    int4 *dst = reinterpret_cast<int4 *>(f + ((int64_t)ih * (ny + 4) + jh) * col_stride);
+    for (int q = lane; q < nchunk; q += 32) dst[q] = src[q];
+    (void)col_bytes;
+}
+
+pw_status pw_launch_halo(const pw_mesh *m, void *const *f, int nf, cudaStream_t st) {
+    int es = pw_elem_in(m->dtype);
+    int64_t col_stride = (int64_t)m->nzp * es;
+    int64_t used = (int64_t)m->nz * es;
+    int nchunk = (int)((used + 15) / 16);
+    int64_t total = 4LL * (m->ny + 4) + 4LL * m->nx;
+    int warps = 8;
+    dim3 grid((unsigned)((total + warps - 1) / warps), (unsigned)nf);
+    char *p0 = (char *)f[0];
+    char *p1 = nf > 1 ? (char *)f[1] : p0;
+    char *p2 = nf > 2 ? (char *)f[2] : p0;
+    pw_halo_kernel<<<grid, warps * 32, 0, st>>>(p0, p1, p2, m->nx, m->ny, used, col_stride, nchunk);
+    PW_CUDA(cudaGetLastError());
+    return PW_OK;
+}
+
+extern "C" pw_status pw_halo_periodic(const pw_mesh *m, void *f1, void *f2, void *f3, void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    pw_status s;
+    if ((s = pw_check_ptr(f1, "f1")) != PW_OK) return s;
+    void *f[3];
+    int n = 0;
+    f[n++] = f1;
+    if (f2) {
+        if ((s = pw_check_ptr(f2, "f2")) != PW_OK) return s;
+        f[n++] = f2;
+    }
+    if (f3) {
+        if ((s = pw_check_ptr(f3, "f3")) != PW_OK) return s;
+        f[n++] = f3;
+    }
+    return pw_launch_halo(m, f, n, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// forward Euler with halo refresh: each interior element is updated once and
+// written to every halo column that is a periodic image of it.
+// ---------------------------------------------------------------------------
+template <typename T, typename TS>
+__global__ void pw_euler_kernel(T *u, T *v, T *w, const TS *su, const TS *sv, const TS *sw,
+                                int nx, int ny, int nz, int nzp, double dt) {
+    T *x = blockIdx.y == 0 ? u : blockIdx.y == 1 ? v : w;
+    const TS *s = blockIdx.y == 0 ? su : blockIdx.y == 1 ? sv : sw;
+    int64_t n = (int64_t)nx * ny * nz;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        int k = (int)(e % nz);
+        int64_t col = e / nz;
+        int j = (int)(col % ny), i = (int)(col / ny);
+        int64_t off = ((int64_t)(i + 2) * (ny + 4) + (j + 2)) * nzp + k;
+        T val = (T)((double)x[off] + dt * (double)s[off]);
+        x[off] = val;
+        bool ei = (i < 2) || (i >= nx - 2), ej = (j < 2) || (j >= ny - 2);
+        if (!ei && !ej) continue;
+        // every halo column (ih, jh) whose periodic image is (i, j)
+        for (int ih = i + 2 - ((i + 2) / nx) * nx; ih < nx + 4; ih += nx) {
+            if (ih < 0) continue;
+            for (int jh = j + 2 - ((j + 2) / ny) * ny; jh < ny + 4; jh += ny) {
+                if (jh < 0) continue;
+                if (ih >= 2 && ih < nx + 2 && jh >= 2 && jh < ny + 2) continue;  // interior
+                x[((int64_t)ih * (ny + 4) + jh) * nzp + k] = val;
+            }
+        }
+    }
+}
+
+// float path: update in FP32 (no double arithmetic)
+template <>
+__global__ void pw_euler_kernel<float, float>(float *u, float *v, float *w, const float *su,
+                                              const float *sv, const float *sw, int nx, int ny,
+                                              int nz, int nzp, double dtd) {
+    float *x = blockIdx.y == 0 ? u : blockIdx.y == 1 ? v : w;
+    const float *s = blockIdx.y == 0 ? su : blockIdx.y == 1 ? sv : sw;
+    float dt = (float)dtd;
+    int64_t n = (int64_t)nx * ny * nz;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        int k = (int)(e % nz);
+        int64_t col = e / nz;
+        int j = (int)(col % ny), i = (int)(col / ny);
+        int64_t off = ((int64_t)(i + 2) * (ny + 4) + (j + 2)) * nzp + k;
+        float val = fmaf(dt, s[off], x[off]);
+        x[off] = val;
+        bool ei = (i < 2) || (i >= nx - 2), ej = (j < 2) || (j >= ny - 2);
+        if (!ei && !ej) continue;
+        for (int ih = i + 2 - ((i + 2) / nx) * nx; ih < nx + 4; ih += nx) {
+            if (ih < 0) continue;
+            for (int jh = j + 2 - ((j + 2) / ny) * ny; jh < ny + 4; jh += ny) {
+                if (jh < 0) continue;
+                if (ih >= 2 && ih < nx + 2 && jh >= 2 && jh < ny + 2) continue;
+                x[((int64_t)ih * (ny + 4) + jh) * nzp + k] = val;
+            }
+        }
+    }
+}
+
+extern "C" pw_status pw_euler(const pw_mesh *m, void *u, void *v, void *w, const void *su,
+                              const void *sv, const void *sw, double dt, void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    pw_status s;
+    const void *ps[6] = {u, v, w, su, sv, sw};
+    const char *nm[6] = {"u", "v", "w", "su", "sv", "sw"};
+    for (int q = 0; q < 6; q++)
+        if ((s = pw_check_ptr(ps[q], nm[q])) != PW_OK) return s;
+    if (!isfinite(dt)) return pw_fail(PW_ERR_ARG, "dt must be finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((unsigned)(m->num_sms * 4), 3);
+    if (m->dtype == PW_F64)
+        pw_euler_kernel<double, double><<<grid, 256, 0, st>>>(
+            (double *)u, (double *)v, (double *)w, (const double *)su, (const double *)sv,
+            (const double *)sw, m->nx, m->ny, m->nz, m->nzp, dt);
+    else if (m->dtype == PW_F32)
+        pw_euler_kernel<float, float><<<grid, 256, 0, st>>>(
+            (float *)u, (float *)v, (float *)w, (const float *)su, (const float *)sv,
+            (const float *)sw, m->nx, m->ny, m->nz, m->nzp, dt);
+    else
+        return pw_fail(PW_ERR_DTYPE, "pw_euler supports PW_F64 and PW_F32 meshes");
+    PW_CUDA(cudaGetLastError());
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A5: FP64 conservation sums, deterministic two-pass tree reduction
+// ---------------------------------------------------------------------------
+template <typename TF, typename TS>
+__global__ void __launch_bounds__(PW_RED_THREADS)
+pw_residual_pass1(const TF *u, const TF *v, const TF *w, const TS *su, const TS *sv, const TS *sw,
+                  const double *wuv, const double *ww, int nx, int ny, int nz, int nzp,
+                  double *partials) {
+    __shared__ double red[12][PW_RED_THREADS];
+    double acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; q++) acc[q] = 0.0;
+    int64_t n = (int64_t)nx * ny * nz;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        int k = (int)(e % nz);
+        int64_t col = e / nz;
+        int j = (int)(col % ny), i = (int)(col / ny);
+        int64_t off = ((int64_t)(i + 2) * (ny + 4) + (j + 2)) * nzp + k;
+        double Wc[3] = {wuv[k], wuv[k], ww[k]};
+        double f[3] = {pw_to<double>(u[off]), pw_to<double>(v[off]), pw_to<double>(w[off])};
+        double s[3] = {(double)su[off], (double)sv[off], (double)sw[off]};
+        if (k == nz - 1) {  // lid face: w and sw are 0 by definition
+            f[2] = 0.0;
+            s[2] = 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            double ps = f[c] * s[c];
+            acc[4 * c + 0] += Wc[c] * ps;
+            acc[4 * c + 1] += Wc[c] * fabs(ps);
+            acc[4 * c + 2] += Wc[c] * s[c];
+            acc[4 * c + 3] += Wc[c] * fabs(s[c]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; q++) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int h = PW_RED_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < 12; q++) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 12) partials[(int64_t)blockIdx.x * 12 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(PW_RED_THREADS)
+pw_residual_pass2(const double *partials, int nblocks, double *out) {
+    __shared__ double red[12][PW_RED_THREADS];
+    for (int q = 0; q < 12; q++) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partials[(int64_t)b * 12 + q];
+        red[q][threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int h = PW_RED_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < 12; q++) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 12) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Launch both passes; `partials` holds PW_RED_BLOCKS*12 doubles and `dout`
+// 12 doubles (both device memory).
+pw_status pw_launch_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
+                              const void *su, const void *sv, const void *sw, double *partials,
+                              double *dout, cudaStream_t st) {
+    const double *wuv = m->coef64 + 10 * m->nz, *ww = m->coef64 + 11 * m->nz;
+#define PW_RES(TF, TS)                                                                         \
+    pw_residual_pass1<TF, TS><<<PW_RED_BLOCKS, PW_RED_THREADS, 0, st>>>(                       \
+        (const TF *)u, (const TF *)v, (const TF *)w, (const TS *)su, (const TS *)sv,           \
+        (const TS *)sw, wuv, ww, m->nx, m->ny, m->nz, m->nzp, partials)
+    if (m->dtype == PW_F64) PW_RES(double, double);
+    else if (m->dtype == PW_F32) PW_RES(float, float);
+    else PW_RES(__nv_bfloat16, float);
+#undef PW_RES
+    PW_CUDA(cudaGetLastError());
+    pw_residual_pass2<<<1, PW_RED_THREADS, 0, st>>>(partials, PW_RED_BLOCKS, dout);
+    PW_CUDA(cudaGetLastError());
+    return PW_OK;
+}
+
+extern "C" pw_status pw_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
+                                  const void *su, const void *sv, const void *sw, double *out,
+                                  void *stream) {
+    if (!m || !out) return pw_fail(PW_ERR_ARG, "mesh and out must not be NULL");
+    pw_status s;
+    const void *ps[6] = {u, v, w, su, sv, sw};
+    const char *nm[6] = {"u", "v", "w", "su", "sv", "sw"};
+    for (int q = 0; q < 6; q++)
+        if ((s = pw_check_ptr(ps[q], nm[q])) != PW_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // scratch: PW_RED_BLOCKS*12 block partials, then the 12 final sums
+    double *final_sums = m->partials + PW_RED_BLOCKS * 12;
+    if ((s = pw_launch_residuals(m, u, v, w, su, sv, sw, m->partials, final_sums, st)) != PW_OK)
+        return s;
+    PW_CUDA(cudaMemcpyAsync(out, final_sums, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PW_CUDA(cudaStreamSynchronize(st));
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// lid check
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void pw_lid_kernel(const T *w, int nx, int ny, int nz, int nzp, int *flag) {
+    int64_t n = (int64_t)nx * ny;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(c % ny), i = (int)(c / ny);
+        T x = w[((int64_t)(i + 2) * (ny + 4) + (j + 2)) * nzp + (nz - 1)];
+        if (pw_to<float>(x) != 0.0f || pw_to<double>(x) != 0.0) atomicOr(flag, 1);
+    }
+}
+
+extern "C" pw_status pw_check_lid(const pw_mesh *m, const void *w, void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    pw_status s;
+    if ((s = pw_check_ptr(w, "w")) != PW_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d = m->status + 1;  // the mesh's lid flag word
+    PW_CUDA(cudaMemsetAsync(d, 0, sizeof(int), st));
+    if (m->dtype == PW_F64) pw_lid_kernel<double><<<m->num_sms * 2, 256, 0, st>>>((const double *)w, m->nx, m->ny, m->nz, m->nzp, d);
+    else if (m->dtype == PW_F32) pw_lid_kernel<float><<<m->num_sms * 2, 256, 0, st>>>((const float *)w, m->nx, m->ny, m->nz, m->nzp, d);
+    else pw_lid_kernel<__nv_bfloat16><<<m->num_sms * 2, 256, 0, st>>>((const __nv_bfloat16 *)w, m->nx, m->ny, m->nz, m->nzp, d);
+    PW_CUDA(cudaGetLastError());
+    int h = 0;
+    PW_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PW_CUDA(cudaStreamSynchronize(st));
+    return h ? pw_fail(PW_ERR_LID, "w has non-zero values on the lid face k = nz-1") : PW_OK;
+}

@@ -1,0 +1,244 @@
+"""GPU parity of the forward path through the C-ABI: coefficients (A1), periodic
+halo fill (A2), the PW stencil in FP64 (A3) and FP32 / BF16 storage (A4), the
+conservation sums (A5), the Euler update and the argument checks that need a
+device.  The reference is the FP64 CPU oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_12850_b300 import synthetic
+
+from parity import TOL_F32_COND, TOL_F64, compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pw():
+    from paper_2009_12850_b300 import build
+    build.build()
+    from paper_2009_12850_b300 import api
+    return api
+
+
+def make(pw, nx, ny, nz, dx=50.0, dy=None, dtype="f64", algo="auto", seed=3, **kw):
+    m = pw.Mesh(nx, ny, nz, dx, dy, dtype=dtype, algo=algo, **kw)
+    u, v, w = synthetic.wind_fields(nx, ny, nz, seed)
+    return m, (u, v, w)
+
+
+def rounded(arrs, dtype):
+    t = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    return [torch.from_numpy(a).to(t).to(torch.float64).numpy() for a in arrs]
+
+
+def run_forward(pw, m, fields, beta=0, init=None):
+    U = [m.from_interior(a) for a in fields]
+    S = [m.empty_out() for _ in range(3)]
+    if init is not None:
+        for s, a in zip(S, init):
+            s.zero_()
+            m.interior(s).copy_(torch.from_numpy(a).to(s.dtype))
+    m.advect(*U, *S, beta=beta)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    return [m.interior(s).double().cpu().numpy() for s in S], U, S
+
+
+SHAPES = [(64, 64, 64), (37, 23, 13), (5, 7, 1), (1, 9, 6), (9, 1, 5), (3, 3, 2), (50, 17, 130),
+          (16, 24, 300)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("algo", ["native"])
+def test_forward_f64(pw, shape, algo):
+    nx, ny, nz = shape
+    m, f = make(pw, nx, ny, nz, dx=50.0, dy=35.0, algo=algo)
+    c = oracle.Coeffs(nz, 50.0, 35.0)
+    (ref, cond) = oracle.advect(c, *f, want_cond=True)
+    got, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        compare(f"s{'uvw'[q]}", got[q], ref[q], cond[q], TOL_F64, TOL_F64)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("shape", [(64, 64, 64), (37, 23, 13), (5, 7, 1), (16, 24, 300), (50, 17, 130)],
+                         ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
+def test_forward_reduced(pw, dtype, shape):
+    nx, ny, nz = shape
+    m, f = make(pw, nx, ny, nz, dx=25.0, dtype=dtype)
+    c = oracle.Coeffs(nz, 25.0, 25.0)
+    fr = rounded(f, dtype)   # the values the kernel actually sees
+    ref, cond = oracle.advect(c, *fr, want_cond=True)
+    got, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        compare(f"{dtype} s{'uvw'[q]}", got[q], ref[q], cond[q], 1e-5, TOL_F32_COND)
+
+
+def test_forward_accumulate(pw):
+    nx, ny, nz = 20, 12, 10
+    m, f = make(pw, nx, ny, nz)
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    rng = np.random.default_rng(1)
+    init = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
+    got, _, _ = run_forward(pw, m, f, beta=1, init=init)
+    for q in range(3):
+        compare("beta=1", got[q] - init[q], ref[q], cond[q] + np.abs(init[q]), 1e-12, 1e-12)
+
+
+def test_outputs_untouched_outside_interior(pw):
+    nx, ny, nz = 12, 10, 13
+    m, f = make(pw, nx, ny, nz, dtype="f32")
+    U = [m.from_interior(a) for a in f]
+    S = [m.empty_out().fill_(7.0) for _ in range(3)]
+    m.advect(*U, *S)
+    torch.cuda.synchronize()
+    for s in S:
+        h = s.cpu().numpy()
+        mask = np.ones(h.shape, bool)
+        mask[2:nx + 2, 2:ny + 2, :nz] = False
+        assert np.all(h[mask] == 7.0)
+
+
+def test_lid_value_ignored(pw):
+    nx, ny, nz = 16, 16, 12
+    m, f = make(pw, nx, ny, nz)
+    u, v, w = f
+    w2 = w.copy()
+    w2[:, :, -1] = 123.0
+    a, _, _ = run_forward(pw, m, (u, v, w))
+    b, _, _ = run_forward(pw, m, (u, v, w2))
+    for q in range(3):
+        assert np.array_equal(a[q], b[q])
+    W = m.from_interior(w2)
+    assert not m.check_lid(W)
+    assert m.check_lid(m.from_interior(w))
+
+
+def test_uniform_flow_exact_zero(pw):
+    nx, ny, nz = 24, 20, 17
+    for dtype in ("f64", "f32", "bf16"):
+        m = pw.Mesh(nx, ny, nz, 40.0, 30.0, dtype=dtype, algo="native")
+        u = np.full((nx, ny, nz), 7.25)
+        v = np.full((nx, ny, nz), -3.5)
+        w = np.zeros((nx, ny, nz))
+        got, _, _ = run_forward(pw, m, (u, v, w))
+        for g in got:
+            assert not g.any(), dtype
+
+
+def test_coefficients_match_oracle(pw):
+    for nz, kw in ((64, {}), (3, {}), (1, {}), (7, {"dz": np.linspace(5, 30, 7), "rho_n": np.linspace(1.2, 0.9, 7),
+                                                      "rho_w": np.linspace(1.19, 0.89, 7)})):
+        m = pw.Mesh(4, 4, nz, 50.0, **kw)
+        c = oracle.Coeffs(nz, 50.0, 50.0, dz=kw.get("dz"), rho_n=kw.get("rho_n"), rho_w=kw.get("rho_w"))
+        g = m.coefficients()
+        for name in ("dz", "zf", "zn", "dzn", "rho_n", "rho_w", "tzc1", "tzc2", "tzd1", "tzd2"):
+            np.testing.assert_allclose(g[name], getattr(c, name), rtol=4e-16 * 8, atol=0, err_msg=name)
+        wuv, ww = oracle.weights(c)
+        np.testing.assert_allclose(g["W_uv"], wuv, rtol=4e-15)
+        np.testing.assert_allclose(g["W_w"], ww, rtol=4e-15)
+        assert g["tcx"] == 0.25 / 50.0
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 5), (1, 1, 3), (2, 3, 9), (1, 5, 4), (33, 2, 17)])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_halo_fill_bit_exact(pw, shape, dtype):
+    nx, ny, nz = shape
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype=dtype)
+    rng = np.random.default_rng(2)
+    a = rng.standard_normal((nx, ny, nz))
+    t = m.from_interior(a, fill_halo=False)
+    m.halo(t)
+    torch.cuda.synchronize()
+    h = t.double().cpu().numpy()
+    ar = torch.from_numpy(a).to(m.in_dtype).double().numpy()
+    ii = (np.arange(nx + 4) - 2) % nx
+    jj = (np.arange(ny + 4) - 2) % ny
+    want = ar[ii][:, jj]
+    assert np.array_equal(h[:, :, :nz], want)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_euler_update_and_halo(pw, dtype):
+    nx, ny, nz = 19, 6, 11
+    m, f = make(pw, nx, ny, nz, dtype=dtype, algo="native")
+    U = [m.from_interior(a) for a in f]
+    S = list(m.advect(*U))
+    before = [m.interior(x).double().cpu().numpy().copy() for x in U]
+    sv = [m.interior(s).double().cpu().numpy() for s in S]
+    m.euler(*U, *S, 0.5)
+    torch.cuda.synchronize()
+    for q in range(3):
+        h = U[q].double().cpu().numpy()
+        want = before[q] + 0.5 * sv[q]
+        got = h[2:nx + 2, 2:ny + 2, :nz]
+        eps = 2.2e-16 if dtype == "f64" else 1.2e-7
+        assert np.all(np.abs(got - want) <= 2 * eps * (np.abs(want) + 1e-30))
+        ii = (np.arange(nx + 4) - 2) % nx
+        jj = (np.arange(ny + 4) - 2) % ny
+        assert np.array_equal(h[:, :, :nz], got[ii][:, jj])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_residual_sums(pw, dtype):
+    nx, ny, nz = 40, 30, 24
+    m, f = make(pw, nx, ny, nz, dtype=dtype, algo="native")
+    U = [m.from_interior(a) for a in f]
+    S = m.advect(*U)
+    gsum = m.residual_sums(*U, *S)
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    fr = [m.interior(x).double().cpu().numpy() for x in U]
+    sr = [m.interior(s).double().cpu().numpy() for s in S]
+    ref = oracle.residual_sums(c, *fr, *sr)
+    # the same products summed in another order: relative to the |.| sums
+    for q in range(3):
+        for t in range(4):
+            den = ref[q, 1] if t < 2 else ref[q, 3]
+            assert abs(gsum[q, t] - ref[q, t]) <= 1e-13 * den, (q, t, gsum[q, t], ref[q, t])
+    # and deterministic run to run
+    again = m.residual_sums(*U, *S)
+    assert np.array_equal(gsum, again)
+    if dtype == "f64":
+        re, rm = m.residuals(*U, *S)
+        assert max(abs(r) for r in re) < 1e-13
+
+
+def test_argument_errors_on_device(pw):
+    from paper_2009_12850_b300 import _lib as L
+    m = pw.Mesh(8, 8, 8, 50.0, dtype="f32")
+    U = [m.zeros() for _ in range(3)]
+    S = [m.empty_out() for _ in range(3)]
+    with pytest.raises(L.PWError) as e:
+        m.advect(*U, *S, beta=2)
+    assert e.value.status == L.PW_ERR_ARG
+    # misaligned pointer
+    big = torch.zeros(m.total + 4, device="cuda")
+    bad = big[1:m.total + 1]
+    with pytest.raises(L.PWError) as e:
+        m.advect(bad, U[1], U[2], *S)
+    assert e.value.status == L.PW_ERR_ALIGN
+    with pytest.raises(L.PWError):
+        m.advect(U[0], U[1], U[2], U[0], S[1], S[2])   # output aliases input
+    with pytest.raises(TypeError):
+        m.advect(U[0].double(), U[1], U[2], *S)
+    with pytest.raises(L.PWError):
+        m.set_tile(0, 32)
+    m64 = pw.Mesh(8, 8, 8, 50.0, dtype="bf16")
+    V = [m64.zeros() for _ in range(3)]
+    with pytest.raises(L.PWError) as e:
+        m64.adjoint(*V, *V, *V)
+    assert e.value.status in (L.PW_ERR_DTYPE, L.PW_ERR_ARG)
+
+
+@pytest.mark.parametrize("tile", [(1, 1), (3, 5), (8, 7), (16, 64), (4, 1000)])
+def test_tiles_do_not_change_results(pw, tile):
+    nx, ny, nz = 45, 29, 20
+    m, f = make(pw, nx, ny, nz, dtype="f32")
+    a, _, _ = run_forward(pw, m, f)
+    m.set_tile(*tile)
+    b, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        assert np.array_equal(a[q], b[q])
