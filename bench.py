@@ -1,0 +1,400 @@
+"""Benchmark of the PW advection hot path on B300.
+
+One STEP = one pass of the per-timestep hot path over the 1024 x 1024 x 128
+synthetic domain (dx = dy = 25 m, stretched dz, anelastic density): periodic
+halo fill of u, v, w followed by the PW stencil u, v, w -> su, sv, sw in FP64
+(the paper's offloaded advection component, sections 2.1 and 3).  The headline
+`value` is advected grid points per second with inputs resident in HBM; `e2e`
+is the same metric through the public API with pinned host buffers (host to
+device copy of u, v, w and device to host copy of su, sv, sw inside every
+step).  Extra objects measure the FP32 and BF16 storage variants on the same
+domain, the native-FP64 kernel, the FP64 conservation reductions, the batched
+ensemble and the adjoint loop.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2009_12850_b300 import synthetic  # noqa: E402
+
+WL = synthetic.LARGE   # replaced by --nx/--ny/--nz for profiling captures of a smaller case
+METRIC = "advected grid points/s (u,v,w) & % HBM roofline; FP32 vs FP64 at stated error"
+UNIT = "points/s"
+BYTES_PER_POINT = {"f64": 48, "f32": 24, "bf16": 18}   # compulsory: read u,v,w + write su,sv,sw
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2009_12850_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".h", ".cuh")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "pwadv.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel_key)
+    if not d or d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[4 + q].lower().startswith("active")})
+        power = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(step, steps, warmup, world, events_for=None):
+    """W untimed steps, then exactly K timed steps between barriers and
+    synchronisations; returns (total seconds of the slowest rank, per-launch ms
+    of the kernel recorded by step())."""
+    import torch
+    for _ in range(warmup):
+        step(None)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    rec = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step(rec)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    total = e0.elapsed_time(e1) / 1e3
+    kern = [a.elapsed_time(b) for a, b in rec]
+    return max_over_ranks(total, world), (float(np.mean(kern)) if kern else None)
+
+
+def run_gpu(args):
+    import torch
+    from paper_2009_12850_b300 import api
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    peaks, peaks_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    nx, ny, nz = WL.nx, WL.ny, WL.nz
+    pts = WL.points
+    u, v, w = synthetic.fields_for(WL)
+
+    def build(dtype, algo="auto"):
+        m = api.Mesh(nx, ny, nz, WL.dx, WL.dy, dtype=dtype, algo=algo, device=dev)
+        U = [m.from_interior(a) for a in (u, v, w)]
+        S = [m.empty_out() for _ in range(3)]
+        return m, U, S
+
+    def make_step(m, U, S):
+        stream = torch.cuda.current_stream()
+
+        def step(rec):
+            m.halo(*U, stream=stream)
+            if rec is None:
+                m.advect(*U, *S, stream=stream)
+            else:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                m.advect(*U, *S, stream=stream)
+                b.record(stream)
+                rec.append((a, b))
+        return step
+
+    # ---------------- headline: FP64 on the device ----------------
+    hd = args.dtype
+    m64, U64, S64 = build(hd, args.algo)
+    with ClockSampler(local) as clk:
+        total, kern_ms = time_steps(make_step(m64, U64, S64), args.steps, args.warmup, world)
+    clocks = clk.summary()
+    assert m64.device_status() == 0, "device wait timed out"
+    value = world * pts * args.steps / total
+    achieved = BYTES_PER_POINT[hd] * pts / (kern_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": recorded_traffic(f"pw_advect_{hd}_{args.algo}"),
+            "kernel": f"pw_advect ({hd}, {args.algo})", "kernel_ms": round(kern_ms, 4),
+            "algorithmic_bytes_per_point": BYTES_PER_POINT[hd], "points_per_launch": pts,
+            "peak_kind": f"{peaks_kind} copy bandwidth"}
+    s64 = [m64.interior(s) for s in S64]
+
+    extras = {}
+    if not args.no_extras and hd == "f64":
+        for dtype, algo_name in (("f32", "auto"), ("bf16", "auto"), ("f64", "native")):
+            m, U, S = build(dtype, algo_name)
+            tot, kms = time_steps(make_step(m, U, S), max(3, args.steps // 2), 3, world)
+            key = dtype if algo_name == "auto" else "f64_native"
+            bpp = BYTES_PER_POINT[dtype]
+            err = {}
+            for q, nm in enumerate(("su", "sv", "sw")):
+                ref = s64[q]
+                d = (m.interior(S[q]).double() - ref).abs()
+                err[nm] = {"max_abs": float(d.max()), "rms": float(d.pow(2).mean().sqrt()),
+                           "rel_to_max": float(d.max() / ref.abs().max())}
+            extras[key] = {"value": world * pts * max(3, args.steps // 2) / tot, "unit": UNIT,
+                           "kernel_ms": round(kms, 4),
+                           "hbm_frac": round(bpp * pts / (kms * 1e-3) / 1e9 / hbm, 4),
+                           "bytes_per_point": bpp, "error_vs_f64_path": err}
+            if key == "f32":
+                extras[key]["speedup_vs_f64"] = round(extras[key]["value"] / value, 3)
+            if key == "f64_native":
+                extras[key]["dp_ops_per_point_est"] = 42
+            del m, U, S
+            torch.cuda.empty_cache()
+        # conservation reductions (A5) on the FP64 fields
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nres = 5
+        for _ in range(nres):
+            sums = m64.residual_sums(*U64, *S64)
+        dt = (time.perf_counter() - t0) / nres
+        re = [float(sums[q, 0] / sums[q, 1]) for q in range(3)]
+        rm = [float(sums[q, 2] / sums[q, 3]) for q in range(3)]
+        extras["residuals"] = {"ms_per_call": round(dt * 1e3, 3), "R_E": re, "R_M": rm}
+
+    # ---------------- e2e: pinned host buffers through the public API --------
+    host_in = [torch.empty(m64.shape, dtype=m64.in_dtype, pin_memory=True) for _ in range(3)]
+    host_out = [torch.empty(m64.shape, dtype=m64.out_dtype, pin_memory=True) for _ in range(3)]
+    for h, d in zip(host_in, U64):
+        h.copy_(d)
+    stream = torch.cuda.current_stream()
+
+    def e2e_step(rec):
+        for h, d in zip(host_in, U64):
+            d.copy_(h, non_blocking=True)
+        m64.halo(*U64, stream=stream)
+        m64.advect(*U64, *S64, stream=stream)
+        for h, d in zip(host_out, S64):
+            h.copy_(d, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 4)
+    e2e_total, _ = time_steps(e2e_step, e2e_steps, 2, world)
+    bytes_in = sum(h.numel() * h.element_size() for h in host_in)
+    bytes_out = sum(h.numel() * h.element_size() for h in host_out)
+    e2e = {"value": world * pts * e2e_steps / e2e_total, "unit": UNIT,
+           "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": hd, "data": "synthetic",
+        "config": {"workload": WL.name, "algo": args.algo, "nx": nx, "ny": ny, "nz": nz, "dx": WL.dx,
+                   "fields": "u,v = 5 + N(0,1) m/s; w = N(0,0.3) m/s, lid 0; dz 10->40 m geometric; "
+                             "rho = 1.2 exp(-z/8000)",
+                   "step": f"halo fill of u,v,w + PW stencil -> su,sv,sw ({hd}, beta=0)",
+                   "l2": "inputs larger than L2 (6.5 GB of fields per step vs 126 MB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "extras": extras,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline leg and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(seconds, ncols=64):
+    """Time the FP64 CPU oracle on slabs of the bench workload (ncols x ny x nz
+    columns of the same field distribution, periodic) until `seconds` of work
+    have run; returns (points/s, threads, description)."""
+    import oracle
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    c = oracle.Coeffs(WL.nz, WL.dx, WL.dy)
+    u, v, w = synthetic.wind_fields(ncols, WL.ny, WL.nz, WL.seed)
+    oracle.advect(c, u, v, w)  # warm
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.advect(c, u, v, w)
+        done += u.size
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return done / el, threads, f"{done // u.size} sweeps of a {ncols}x{WL.ny}x{WL.nz} slab " \
+                               f"({done} points, {el:.1f} s)"
+
+
+def cpu_baseline(seconds):
+    rate, threads, desc = oracle_sample(seconds)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": desc + "; FP64 C oracle, OpenMP over x"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    rates = []
+    for _ in range(args.warmup):
+        oracle_sample(min(per_step, 5.0))
+    t0 = time.perf_counter()
+    descs = []
+    for _ in range(args.steps):
+        r, threads, d = oracle_sample(per_step)
+        rates.append(r)
+        descs.append(d)
+    total = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WL.name, "nx": WL.nx, "ny": WL.ny, "nz": WL.nz, "dx": WL.dx,
+                       "step": "PW stencil u,v,w -> su,sv,sw (FP64) on a bounded slab sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": descs[-1]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="only the headline and e2e")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64", help="headline storage type")
+    ap.add_argument("--algo", choices=["auto", "native", "split"], default="auto", help="FP64 arithmetic")
+    ap.add_argument("--nx", type=int, default=None, help="smaller domain (ncu captures)")
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--nz", type=int, default=None)
+    args = ap.parse_args()
+    global WL
+    if args.nx or args.ny or args.nz:
+        nx, ny, nz = args.nx or WL.nx, args.ny or WL.ny, args.nz or WL.nz
+        WL = synthetic.Workload(f"pw_{nx}x{ny}x{nz}_dx25", nx, ny, nz, WL.dx, WL.dy, WL.seed)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

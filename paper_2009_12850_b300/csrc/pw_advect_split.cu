@@ -1,0 +1,292 @@
+// pw_advect_split.cu -- FP64 PW stencil in double-float arithmetic (FP64 in,
+// FP64 out, error within a few units of 2^-46 of the per-point condition sum).
+//
+// Why: B300's FP64 units run at ~1.6 operations / clock / SM, so native FP64
+// caps this ~42-FLOP-per-point stencil near 11 Gpoints/s (8% of the HBM
+// roofline).  Here every double is split exactly-enough into two floats and the
+// stencil runs on the FP32 pipe (packed .f32x2 instructions over two k levels),
+// with FP64 used only for one add per output.
+//
+// Layout of the work: the same x-march as the FP32 kernel.  A CTA owns tile_j
+// rows and a k chunk; TMA brings (j,k) planes of u, v, w (doubles) into a ring
+// of NS shared-memory slots; when a plane has landed, all threads convert it in
+// place, 16 bytes at a time, from (x_k, x_k+1) to (hi_k, hi_k+1, lo_k, lo_k+1),
+// zeroing the padding (k >= nz) and the w lid (k = nz-1) on the way.  Each
+// thread then computes two levels (k, k+1) of one column per step.
+//
+// The algebra is the PW form regrouped around the face coefficients:
+//   tzc1(k) = g(k-1) r(k), tzc2(k) = g(k) r(k),   g = 0.25 rho_w, r = 1/(rho_n dz)
+//   tzd1(k) = g'(k) r'(k), tzd2(k) = g'(k+1) r'(k), g' = 0.25 rho_n, r' = 1/(rho_w dzn)
+// so that  s = tcx X + tcy Y + r Z  with X, Y, Z differences of products of a
+// field value and an (unscaled, or g-scaled for the vertical) face sum.
+#include <algorithm>
+
+#include "pw_df.cuh"
+#include "pw_internal.h"
+
+struct PwSplitGeom {
+    int nx, ny, nz, kc, kb, tj, ti;
+    int rows;          // 3 * (tj + 2) rows per plane (u, v, w)
+    int cpr;           // 16-byte chunks per plane row = kb / 2
+    float inv_cpr;
+    int field_stride;  // doubles between the u, v, w planes of a slot
+    int cs_n;          // levels in the coefficient table (nz + 4, level -2 first)
+    long long si, sj;
+};
+
+// coefficient table (floats): 8 arrays of cs_n levels starting at level -2:
+// g_h g_l gp_h gp_l r_h r_l rp_h rp_l, then tcx_h tcx_l tcy_h tcy_l
+__device__ __forceinline__ D2 cs_pair(const float *cs, int n, int arr, int k) {
+    const float *h = cs + (2 * arr) * n + k + 2;
+    const float *l = cs + (2 * arr + 1) * n + k + 2;
+    return D2{pk(h[0], h[1]), pk(l[0], l[1])};
+}
+
+// D2 of levels (k+s, k+1+s), s in {-1, 0, 1}, from a converted plane row
+template <int S>
+__device__ __forceinline__ D2 ld2(const double *row, int kk) {
+    const float4 c = *reinterpret_cast<const float4 *>(row + kk);
+    if (S == 0) return D2{pk(c.x, c.y), pk(c.z, c.w)};
+    if (S < 0) {
+        const float4 m = *reinterpret_cast<const float4 *>(row + kk - 2);
+        return D2{pk(m.y, c.x), pk(m.w, c.z)};
+    }
+    const float4 p = *reinterpret_cast<const float4 *>(row + kk + 2);
+    return D2{pk(c.y, p.x), pk(c.w, p.z)};
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256, 2)
+pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
+                       const __grid_constant__ CUtensorMap mw, double *__restrict__ su,
+                       double *__restrict__ sv, double *__restrict__ sw,
+                       const float *__restrict__ cs, const PwSplitGeom g, int beta,
+                       int *__restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    double *planes = reinterpret_cast<double *>(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * 3 * g.field_stride * 8);
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int nkt = g.kc / 2;
+    const int tk = tid % nkt, tj = tid / nkt;
+    const int j0 = blockIdx.x * g.tj, i0 = blockIdx.y * g.ti, k0 = blockIdx.z * g.kc;
+    const int i_end = min(i0 + g.ti, g.nx);
+    const int nplanes = i_end - i0 + 2;
+    const uint32_t plane_bytes = 3u * (uint32_t)(g.tj + 2) * (uint32_t)g.kb * 8u;
+    const int kbase = k0 + 2 * tk, kk = 2 + 2 * tk, j = j0 + tj;
+    const int fs = g.field_stride;
+
+    if (pw_status_failed(status)) return;
+    if (tid == 0) {
+        pw_prefetch_map(&mu);
+        pw_prefetch_map(&mv);
+        pw_prefetch_map(&mw);
+        for (int s = 0; s < NS; s++) pw_mbar_init(&bars[s], 1);
+        pw_fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](int p) {
+        const int s = p % NS;
+        double *dst = planes + (size_t)s * 3 * fs;
+        pw_mbar_expect_tx(&bars[s], plane_bytes);
+        const int c0 = k0 - 2, c1 = j0 + 1, c2 = i0 + 1 + p;
+        pw_tma_load_3d(dst, &mu, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + fs, &mv, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + 2 * fs, &mw, c0, c1, c2, &bars[s]);
+    };
+    int issued = 0;
+    if (tid == 0) {
+        for (int p = 0; p < min(NS, nplanes); p++) issue(p);
+        issued = min(NS, nplanes);
+    }
+    auto wait = [&](int p) {
+        return pw_mbar_wait_bounded(&bars[p % NS], (uint32_t)((p / NS) & 1));
+    };
+    auto give_up = [&](int from) {
+        if (tid == 0) {
+            for (int p = from; p < issued; p++)
+                if (!pw_mbar_wait_bounded(&bars[p % NS], (uint32_t)((p / NS) & 1), PW_DRAIN_CYCLES)) break;
+            atomicExch(status, (int)PW_ERR_TIMEOUT);
+        }
+    };
+    // in-place conversion of a landed plane: doubles -> (hi, hi, lo, lo) chunks
+    auto convert = [&](int p) {
+        double *base = planes + (size_t)(p % NS) * 3 * fs;
+        const int total = g.rows * g.cpr, rpf = g.tj + 2;
+        for (int c = tid; c < total; c += nt) {
+            const int row = (int)(((float)c + 0.5f) * g.inv_cpr);
+            const int q = c - row * g.cpr;
+            const int f = (row >= rpf) + (row >= 2 * rpf);
+            const int r = row - f * rpf;
+            double *cp = base + (size_t)f * fs + (size_t)r * g.kb + 2 * q;
+            double2 d = *reinterpret_cast<const double2 *>(cp);
+            const int klev = k0 - 2 + 2 * q;
+            const int kz = (f == 2) ? g.nz - 1 : g.nz;
+            if (klev >= kz) d.x = 0.0;
+            if (klev + 1 >= kz) d.y = 0.0;
+            float h0, l0, h1, l1;
+            split_double(d.x, h0, l0);
+            split_double(d.y, h1, l1);
+            *reinterpret_cast<float4 *>(cp) = make_float4(h0, h1, l0, l1);
+        }
+    };
+
+    // per-thread coefficients for levels (k, k+1) and their shifts
+    const int N = g.cs_n;
+    const int kq = min(kbase, g.nz - 1);  // threads past the top only read valid entries
+    const D2 Gm = cs_pair(cs, N, 0, kq - 1), G0 = cs_pair(cs, N, 0, kq);
+    const D2 GP0 = cs_pair(cs, N, 1, kq), GPp = cs_pair(cs, N, 1, kq + 1);
+    const D2 R0 = cs_pair(cs, N, 2, kq), RP0 = cs_pair(cs, N, 3, kq);
+    const float *tc = cs + 8 * N;
+    const D2 TCX{pk(tc[0], tc[0]), pk(tc[1], tc[1])}, TCY{pk(tc[2], tc[2]), pk(tc[3], tc[3])};
+    const bool active = (j < g.ny) && (kbase < g.nz);
+
+    // planes i0-1 and i0
+    {
+        const bool ok = wait(0) && wait(1);  // nplanes >= 3 always
+        if (ok) {
+            convert(0);
+            convert(1);
+        }
+        if (!__syncthreads_and(ok)) {
+            give_up(0);
+            return;
+        }
+    }
+    D2 Fx_m, Gx_m, Hx_m;
+    bool first = true;
+    for (int i = i0; i < i_end; i++) {
+        const int q = i - i0 + 1;
+        bool ok = wait(q + 1);
+        if (ok) convert(q + 1);
+        if (!__syncthreads_and(ok)) {
+            give_up(q + 1);
+            return;
+        }
+        if (tid == 0 && q >= 2 && q - 2 + NS < nplanes) {
+            issue(q - 2 + NS);
+            issued = q - 1 + NS;
+        }
+        if (!active) continue;
+
+        const double *Pm = planes + (size_t)((q - 1) % NS) * 3 * fs;
+        const double *Pc = planes + (size_t)(q % NS) * 3 * fs;
+        const double *Pp = planes + (size_t)((q + 1) % NS) * 3 * fs;
+        const int rS = tj * g.kb, rC = (tj + 1) * g.kb, rN = (tj + 2) * g.kb;
+        const double *uM = Pm + rC, *uC = Pc + rC, *uP = Pp + rC;
+        const double *vMr = Pm + fs + rC, *vCr = Pc + fs + rC, *vPr = Pp + fs + rC;
+        const double *wMr = Pm + 2 * fs + rC, *wCr = Pc + 2 * fs + rC, *wPr = Pp + 2 * fs + rC;
+
+        // ---------------- su ----------------
+        const D2 uM0 = ld2<0>(uM, kk), uC0 = ld2<0>(uC, kk), uP0 = ld2<0>(uP, kk);
+        if (first) Fx_m = df_add(uM0, uC0);
+        const D2 Fx_p = df_add(uC0, uP0);
+        D2 X = df_mul(df_sub(df_mul(uM0, Fx_m), df_mul(uP0, Fx_p)), TCX);
+        const D2 uS0 = ld2<0>(Pc + rS, kk), uN0 = ld2<0>(Pc + rN, kk);
+        const D2 vS0 = ld2<0>(Pc + fs + rS, kk), vSP0 = ld2<0>(Pp + fs + rS, kk);
+        const D2 vC0 = ld2<0>(vCr, kk), vP0 = ld2<0>(vPr, kk);
+        D2 Y = df_mul(df_sub(df_mul(uS0, df_add(vS0, vSP0)), df_mul(uN0, df_add(vC0, vP0))), TCY);
+        const D2 wCm = ld2<-1>(wCr, kk), wPm = ld2<-1>(wPr, kk);
+        const D2 wC0 = ld2<0>(wCr, kk), wP0 = ld2<0>(wPr, kk);
+        const D2 uCm = ld2<-1>(uC, kk), uCp = ld2<1>(uC, kk);
+        D2 Z = df_mul(df_sub(df_mul(uCm, df_mul(df_add(wCm, wPm), Gm)),
+                             df_mul(uCp, df_mul(df_add(wC0, wP0), G0))), R0);
+        const D2 ru = df_add(df_add(X, Y), Z);
+
+        // ---------------- sv ----------------
+        const D2 vM0 = ld2<0>(vMr, kk), uNM0 = ld2<0>(Pm + rN, kk);
+        if (first) Gx_m = df_add(uM0, uNM0);
+        const D2 Gx_p = df_add(uC0, uN0);
+        X = df_mul(df_sub(df_mul(vM0, Gx_m), df_mul(vP0, Gx_p)), TCX);
+        const D2 vN0 = ld2<0>(Pc + fs + rN, kk);
+        Y = df_mul(df_sub(df_mul(vS0, df_add(vS0, vC0)), df_mul(vN0, df_add(vC0, vN0))), TCY);
+        const D2 wNm = ld2<-1>(Pc + 2 * fs + rN, kk), wN0 = ld2<0>(Pc + 2 * fs + rN, kk);
+        const D2 vCm = ld2<-1>(vCr, kk), vCp = ld2<1>(vCr, kk);
+        Z = df_mul(df_sub(df_mul(vCm, df_mul(df_add(wCm, wNm), Gm)),
+                          df_mul(vCp, df_mul(df_add(wC0, wN0), G0))), R0);
+        const D2 rv = df_add(df_add(X, Y), Z);
+
+        // ---------------- sw ----------------
+        const D2 wM0 = ld2<0>(wMr, kk), uMp = ld2<1>(uM, kk);
+        if (first) Hx_m = df_add(uM0, uMp);
+        const D2 Hx_p = df_add(uC0, uCp);
+        X = df_mul(df_sub(df_mul(wM0, Hx_m), df_mul(wP0, Hx_p)), TCX);
+        const D2 wS0 = ld2<0>(Pc + 2 * fs + rS, kk), vSp = ld2<1>(Pc + fs + rS, kk);
+        Y = df_mul(df_sub(df_mul(wS0, df_add(vS0, vSp)), df_mul(wN0, df_add(vC0, vCp))), TCY);
+        const D2 wCp = ld2<1>(wCr, kk);
+        Z = df_mul(df_sub(df_mul(wCm, df_mul(df_add(wCm, wC0), GP0)),
+                          df_mul(wCp, df_mul(df_add(wC0, wCp), GPp))), RP0);
+        const D2 rw = df_add(df_add(X, Y), Z);
+
+        Fx_m = Fx_p;
+        Gx_m = Gx_p;
+        Hx_m = Hx_p;
+        first = false;
+
+        // ---------------- outputs ----------------
+        const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
+        double a0 = join(lx(ru.h), lx(ru.l)), a1 = join(ly(ru.h), ly(ru.l));
+        double b0 = join(lx(rv.h), lx(rv.l)), b1 = join(ly(rv.h), ly(rv.l));
+        double c0 = join(lx(rw.h), lx(rw.l)), c1 = join(ly(rw.h), ly(rw.l));
+        if (kbase >= g.nz - 1) c0 = 0.0;
+        if (kbase + 1 >= g.nz - 1) c1 = 0.0;
+        if (kbase + 1 < g.nz) {
+            double2 *pu = reinterpret_cast<double2 *>(su + off);
+            double2 *pv = reinterpret_cast<double2 *>(sv + off);
+            double2 *pw = reinterpret_cast<double2 *>(sw + off);
+            if (beta) {
+                const double2 ou = *pu, ov = *pv, ow = *pw;
+                a0 += ou.x; a1 += ou.y; b0 += ov.x; b1 += ov.y; c0 += ow.x; c1 += ow.y;
+            }
+            *pu = make_double2(a0, a1);
+            *pv = make_double2(b0, b1);
+            *pw = make_double2(c0, c1);
+        } else {
+            su[off] = beta ? su[off] + a0 : a0;
+            sv[off] = beta ? sv[off] + b0 : b0;
+            sw[off] = beta ? sw[off] + c0 : c0;
+        }
+    }
+}
+
+pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v, const void *w,
+                                 void *su, void *sv, void *sw, int beta, cudaStream_t st,
+                                 int tile_j, int tile_i) {
+    constexpr int NS = 5;
+    PwSplitGeom g;
+    g.nx = m->nx;
+    g.ny = m->ny;
+    g.nz = m->nz;
+    const int kc_one = (m->nz + 1) / 2 * 2;
+    g.kc = kc_one <= 64 ? kc_one : 64;
+    g.kb = g.kc + 4;
+    g.tj = tile_j;
+    g.ti = tile_i;
+    g.rows = 3 * (tile_j + 2);
+    g.cpr = g.kb / 2;
+    g.inv_cpr = 1.0f / (float)g.cpr;
+    const int plane_elems = (tile_j + 2) * g.kb;
+    g.field_stride = (plane_elems + 15) / 16 * 16;  // 128-byte aligned planes
+    g.cs_n = m->nz + 4;
+    g.si = m->si;
+    g.sj = m->sj;
+    const int threads = (g.kc / 2) * tile_j;
+    if (threads > 256)
+        return pw_fail(PW_ERR_SHAPE, "split kernel: tile_j=%d needs %d threads (max 256)", tile_j, threads);
+    const size_t smem = (size_t)NS * 3 * g.field_stride * 8 + NS * sizeof(uint64_t);
+    if (smem > 227 * 1024) return pw_fail(PW_ERR_SHAPE, "split kernel needs %zu bytes of shared memory", smem);
+    CUtensorMap maps[3];
+    const void *f[3] = {u, v, w};
+    for (int q = 0; q < 3; q++) {
+        pw_status s = pw_make_field_map(&maps[q], f[q], PW_F64, m->nx, m->ny, m->nzp, g.kb, tile_j + 2);
+        if (s != PW_OK) return s;
+    }
+    auto kern = pw_advect_split_kernel<NS>;
+    PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
+              (unsigned)((m->nz + g.kc - 1) / g.kc));
+    if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");
+    kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (double *)su, (double *)sv, (double *)sw,
+                                      m->coefsplit, g, beta, m->status);
+    PW_CUDA(cudaGetLastError());
+    return PW_OK;
+}

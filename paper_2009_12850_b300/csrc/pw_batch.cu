@@ -1,13 +1,6 @@
 // pw_batch.cu -- batched ensembles and the tile autotuner (being written).
 #include "pw_internal.h"
 
-pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v, const void *w,
-                                 void *su, void *sv, void *sw, int beta, cudaStream_t st,
-                                 int tile_j, int tile_i) {
-    (void)m; (void)u; (void)v; (void)w; (void)su; (void)sv; (void)sw; (void)beta; (void)st;
-    (void)tile_j; (void)tile_i;
-    return pw_fail(PW_ERR_DTYPE, "PW_ALGO_F64_SPLIT is not built yet");
-}
 extern "C" pw_status pw_batch_create(pw_mesh *const *, int, void *, pw_batch **out) {
     if (out) *out = nullptr;
     return pw_fail(PW_ERR_DTYPE, "batches are not built yet");

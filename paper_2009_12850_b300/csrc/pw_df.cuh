@@ -1,0 +1,127 @@
+// pw_df.cuh -- packed double-float arithmetic for the FP64 "split" stencil.
+//
+// A double x is carried as an unevaluated pair of floats (hi, lo) with
+// x = hi + lo + d, |d| <= 2^-46 |x|.  Two consecutive k levels are processed
+// together in Blackwell's packed FP32 instructions (add/sub/mul/fma .f32x2),
+// so a P2 holds (level k, level k+1) and a D2 holds the hi and lo parts of two
+// levels.  Arithmetic follows the classical error-free transformations:
+//   TwoSum (Knuth):    s = a + b, e = (a - (s - bb)) + (b - bb), bb = s - a,
+//                      a + b = s + e exactly;
+//   TwoProd (FMA):     p = a * b, e = fma(a, b, -p),  a * b = p + e exactly;
+// and the "lazy" double-float add and multiply built on them, which skip the
+// final renormalisation: their results stay accurate to a few units of 2^-46
+// relative to the sum of the magnitudes involved, which is what the stencil's
+// error bound (1e-12 of the per-point condition sum) needs.
+//
+// Conversions avoid the FP64 pipe (f64<->f32 conversions run at the DP rate on
+// B300): doubles are split with integer bit operations, and results are
+// rebuilt from (hi, lo) with integer widening plus one FP64 add.
+#pragma once
+
+#include <stdint.h>
+
+struct P2 {
+    unsigned long long v;
+};
+struct D2 {
+    P2 h, l;
+};
+
+__device__ __forceinline__ P2 pk(float a, float b) {
+    P2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lx(P2 a) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return x;
+}
+__device__ __forceinline__ float ly(P2 a) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return y;
+}
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) {
+    P2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) {
+    P2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ P2 operator*(P2 a, P2 b) {
+    P2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ P2 pfma(P2 a, P2 b, P2 c) {
+    P2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// a*b = p + e exactly (the error by scalar FMAs, which negate for free)
+__device__ __forceinline__ P2 two_prod_err(P2 a, P2 b, P2 p) {
+    return pk(fmaf(lx(a), lx(b), -lx(p)), fmaf(ly(a), ly(b), -ly(p)));
+}
+
+// lazy double-float sum / difference: TwoSum of the hi parts, lo parts added
+__device__ __forceinline__ D2 df_add(D2 a, D2 b) {
+    P2 s = a.h + b.h;
+    P2 bb = s - a.h;
+    P2 e = (a.h - (s - bb)) + (b.h - bb);
+    return D2{s, e + (a.l + b.l)};
+}
+__device__ __forceinline__ D2 df_sub(D2 a, D2 b) {
+    P2 s = a.h - b.h;
+    P2 bb = s - a.h;
+    P2 e = (a.h - (s - bb)) - (b.h + bb);
+    return D2{s, e + (a.l - b.l)};
+}
+// lazy double-float product (the lo*lo term is below 2^-46 and dropped)
+__device__ __forceinline__ D2 df_mul(D2 a, D2 b) {
+    P2 p = a.h * b.h;
+    P2 e = two_prod_err(a.h, b.h, p);
+    e = pfma(a.h, b.l, e);
+    e = pfma(a.l, b.h, e);
+    return D2{p, e};
+}
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+// Split a double into (hi, lo): hi = x truncated to 24 significant bits, lo =
+// the next 23 bits (exact float subtraction of the implicit bit), so
+// |x - hi - lo| < 2^-46 |x|.  Integer operations only.  Values with
+// |x| < 2^-100 (and zeros) give (0, 0); |x| must be below 2^127.
+__device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
+    const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+    // top 23 mantissa bits and the low 8 exponent bits, then rebias 1023 -> 127
+    const uint32_t f = __funnelshift_l(xl, xh, 3) ^ 0x40000000u;
+    const uint32_t hb = (f & 0x7fffffffu) | (xh & 0x80000000u);
+    // lo: 1.m x 2^(e-23) minus 2^(e-23), with m the next 23 mantissa bits
+    const uint32_t cb = (hb & 0xff800000u) - 0x0b800000u;
+    const uint32_t fb = cb | ((xl >> 6) & 0x007fffffu);
+    const bool tiny = (xh & 0x7ff00000u) < 0x39b00000u;  // biased exponent < 923
+    hi = tiny ? 0.0f : __uint_as_float(hb);
+    lo = tiny ? 0.0f : __uint_as_float(fb) - __uint_as_float(cb);
+}
+
+// Exact float -> double by integer widening (zeros and subnormals -> +-0).
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t a = b & 0x7fffffffu;
+    uint32_t h = ((a >> 3) + 0x38000000u) | (b & 0x80000000u);
+    uint32_t l = a << 29;
+    if (a < 0x00800000u) {
+        h = b & 0x80000000u;
+        l = 0u;
+    }
+    return __hiloint2double((int)h, (int)l);
+}
+
+// hi + lo rounded to double (one FP64 add)
+__device__ __forceinline__ double join(float hi, float lo) { return widen(hi) + widen(lo); }

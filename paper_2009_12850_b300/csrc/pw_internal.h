@@ -22,6 +22,7 @@ struct pw_mesh {
     int num_sms;
     double *coef64;          // device, 12*nz: dz zf zn dzn rho_n rho_w tzc1 tzc2 tzd1 tzd2 Wuv Ww
     float *coef32;           // device, 4*nz: tzc1 tzc2 tzd1 tzd2
+    float *coefsplit;        // device, 8*(nz+4)+4: float pairs of g, g', r, r' (levels -2..nz+1), tcx, tcy
     double *partials;        // device, residual scratch: (PW_RED_BLOCKS + 1) * 12 doubles
     int *status;             // device: [0] timeout status (0 or PW_ERR_TIMEOUT), [1] lid flag
     int tile_j, tile_i;      // stencil tile: rows per CTA, columns marched per CTA

@@ -146,10 +146,42 @@ __global__ void pw_coeffs_kernel(int nz, const double *dz_in, const double *rn_i
     }
 }
 
+// Float-pair table for the FP64 split kernel: the vertical coefficients are
+// regrouped as tzc1(k) = g(k-1) r(k), tzc2(k) = g(k) r(k), tzd1(k) = g'(k) r'(k),
+// tzd2(k) = g'(k+1) r'(k) with g = 0.25 rho_w, g' = 0.25 rho_n, r = 1/(rho_n dz),
+// r' = 1/(rho_w dzn) (0 on the lid face), each stored as hi + lo floats for
+// levels -2 .. nz+1 (0 outside 0..nz-1), followed by tcx and tcy.
+__global__ void pw_coeffs_split_kernel(int nz, const double *c64, double tcx, double tcy, float *cs) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const double *dz = c64, *dzn = c64 + 3 * nz, *rn = c64 + 4 * nz, *rw = c64 + 5 * nz;
+    const int n = nz + 4;
+    for (int q = 0; q < n; q++) {
+        const int k = q - 2;
+        const bool in = k >= 0 && k < nz;
+        double v[4];
+        v[0] = in ? 0.25 * rw[k] : 0.0;
+        v[1] = in ? 0.25 * rn[k] : 0.0;
+        v[2] = in ? 1.0 / (rn[k] * dz[k]) : 0.0;
+        v[3] = (in && k < nz - 1) ? 1.0 / (rw[k] * dzn[k]) : 0.0;
+        for (int a = 0; a < 4; a++) {
+            const float h = (float)v[a];
+            cs[(2 * a) * n + q] = h;
+            cs[(2 * a + 1) * n + q] = (float)(v[a] - (double)h);
+        }
+    }
+    const double t[2] = {tcx, tcy};
+    for (int a = 0; a < 2; a++) {
+        const float h = (float)t[a];
+        cs[8 * n + 2 * a] = h;
+        cs[8 * n + 2 * a + 1] = (float)(t[a] - (double)h);
+    }
+}
+
 static void pw_mesh_free(pw_mesh *m) {
     if (!m) return;
     cudaFree(m->coef64);
     cudaFree(m->coef32);
+    cudaFree(m->coefsplit);
     cudaFree(m->partials);
     cudaFree(m->status);
     free(m);
@@ -196,7 +228,7 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
     m->tcx = 0.25 / d->dx;
     m->tcy = 0.25 / d->dy;
     m->dtype = d->dtype;
-    m->algo = d->algo == PW_ALGO_AUTO ? PW_ALGO_F64_NATIVE : d->algo;
+    m->algo = d->algo == PW_ALGO_AUTO ? PW_ALGO_F64_SPLIT : d->algo;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&m->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
@@ -204,11 +236,12 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
         pw_mesh_free(m);
         return pw_cuda_fail(e, "device query");
     }
-    m->tile_j = d->dtype == PW_F64 ? 4 : 8;
+    m->tile_j = (d->dtype == PW_F64 && m->algo == PW_ALGO_F64_NATIVE) ? 4 : 8;
     m->tile_i = 32;
     double *tmp = nullptr;
     if ((e = cudaMalloc(&m->coef64, 12 * (size_t)nz * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&m->coef32, 4 * (size_t)nz * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&m->coefsplit, (8 * ((size_t)nz + 4) + 4) * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&m->partials, (PW_RED_BLOCKS + 1) * 12 * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&m->status, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&tmp, 3 * (size_t)nz * sizeof(double))) != cudaSuccess) {
@@ -225,6 +258,8 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
         pw_coeffs_kernel<<<1, 32, 0, st>>>(nz, tmp, tmp + nz, tmp + 2 * nz, d->dz != nullptr,
                                            d->rho_n != nullptr, d->rho_w != nullptr, rho0, H,
                                            m->coef64, m->coef32);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        pw_coeffs_split_kernel<<<1, 32, 0, st>>>(nz, m->coef64, m->tcx, m->tcy, m->coefsplit);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         e = cudaStreamSynchronize(st);
     } while (0);

@@ -51,7 +51,7 @@ SHAPES = [(64, 64, 64), (37, 23, 13), (5, 7, 1), (1, 9, 6), (9, 1, 5), (3, 3, 2)
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("algo", ["native"])
+@pytest.mark.parametrize("algo", ["native", "split"])
 def test_forward_f64(pw, shape, algo):
     nx, ny, nz = shape
     m, f = make(pw, nx, ny, nz, dx=50.0, dy=35.0, algo=algo)
@@ -76,9 +76,10 @@ def test_forward_reduced(pw, dtype, shape):
         compare(f"{dtype} s{'uvw'[q]}", got[q], ref[q], cond[q], 1e-5, TOL_F32_COND)
 
 
-def test_forward_accumulate(pw):
-    nx, ny, nz = 20, 12, 10
-    m, f = make(pw, nx, ny, nz)
+@pytest.mark.parametrize("algo", ["native", "split"])
+def test_forward_accumulate(pw, algo):
+    nx, ny, nz = 20, 12, 11
+    m, f = make(pw, nx, ny, nz, algo=algo)
     c = oracle.Coeffs(nz, 50.0, 50.0)
     ref, cond = oracle.advect(c, *f, want_cond=True)
     rng = np.random.default_rng(1)
@@ -102,9 +103,10 @@ def test_outputs_untouched_outside_interior(pw):
         assert np.all(h[mask] == 7.0)
 
 
-def test_lid_value_ignored(pw):
+@pytest.mark.parametrize("algo", ["native", "split"])
+def test_lid_value_ignored(pw, algo):
     nx, ny, nz = 16, 16, 12
-    m, f = make(pw, nx, ny, nz)
+    m, f = make(pw, nx, ny, nz, algo=algo)
     u, v, w = f
     w2 = w.copy()
     w2[:, :, -1] = 123.0
@@ -119,8 +121,8 @@ def test_lid_value_ignored(pw):
 
 def test_uniform_flow_exact_zero(pw):
     nx, ny, nz = 24, 20, 17
-    for dtype in ("f64", "f32", "bf16"):
-        m = pw.Mesh(nx, ny, nz, 40.0, 30.0, dtype=dtype, algo="native")
+    for dtype, algo in (("f64", "native"), ("f64", "split"), ("f32", "auto"), ("bf16", "auto")):
+        m = pw.Mesh(nx, ny, nz, 40.0, 30.0, dtype=dtype, algo=algo)
         u = np.full((nx, ny, nz), 7.25)
         v = np.full((nx, ny, nz), -3.5)
         w = np.zeros((nx, ny, nz))
@@ -242,3 +244,32 @@ def test_tiles_do_not_change_results(pw, tile):
     b, _, _ = run_forward(pw, m, f)
     for q in range(3):
         assert np.array_equal(a[q], b[q])
+
+
+@pytest.mark.parametrize("scale", [1e-6, 1e-3, 1.0, 1e3, 1e9])
+def test_split_magnitude_range(pw, scale):
+    """The split path keeps 1e-12 of the condition sum for field magnitudes
+    across its documented range, with mixed signs and exact zeros."""
+    nx, ny, nz = 24, 20, 18
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo="split")
+    rng = np.random.default_rng(21)
+    f = [scale * rng.standard_normal((nx, ny, nz)) * np.exp(rng.uniform(-3, 3, (nx, ny, nz))) for _ in range(3)]
+    f[0][::3, ::2, ::5] = 0.0
+    f[2][:, :, -1] = 0.0
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    got, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        compare(f"split x{scale:g} s{'uvw'[q]}", got[q], ref[q], cond[q], TOL_F64, TOL_F64)
+
+
+@pytest.mark.parametrize("tile", [(1, 1), (3, 5), (8, 7), (4, 1000), (2, 64)])
+def test_split_tiles(pw, tile):
+    nx, ny, nz = 45, 29, 70
+    m, f = make(pw, nx, ny, nz, algo="split")
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    m.set_tile(*tile)
+    got, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        compare("split tile", got[q], ref[q], cond[q], TOL_F64, TOL_F64)
