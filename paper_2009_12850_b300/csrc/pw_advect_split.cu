@@ -55,12 +55,12 @@ __device__ __forceinline__ D2 ld2(const double *row, int kk) {
     return D2{pk(c.y, p.x), pk(c.w, p.z)};
 }
 
-template <int NS>
+template <int NS, int TJ, bool BETA>
 __global__ void __launch_bounds__(256, 2)
 pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                        const __grid_constant__ CUtensorMap mw, double *__restrict__ su,
                        double *__restrict__ sv, double *__restrict__ sw,
-                       const float *__restrict__ cs, const PwSplitGeom g, int beta,
+                       const float *__restrict__ cs, const PwSplitGeom g,
                        int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double *planes = reinterpret_cast<double *>(smem_raw);
@@ -68,10 +68,10 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     const int nt = blockDim.x, tid = threadIdx.x;
     const int nkt = g.kc / 2;
     const int tk = tid % nkt, tj = tid / nkt;
-    const int j0 = blockIdx.x * g.tj, i0 = blockIdx.y * g.ti, k0 = blockIdx.z * g.kc;
+    const int j0 = blockIdx.x * TJ, i0 = blockIdx.y * g.ti, k0 = blockIdx.z * g.kc;
     const int i_end = min(i0 + g.ti, g.nx);
     const int nplanes = i_end - i0 + 2;
-    const uint32_t plane_bytes = 3u * (uint32_t)(g.tj + 2) * (uint32_t)g.kb * 8u;
+    const uint32_t plane_bytes = 3u * (uint32_t)(TJ + 2) * (uint32_t)g.kb * 8u;
     const int kbase = k0 + 2 * tk, kk = 2 + 2 * tk, j = j0 + tj;
     const int fs = g.field_stride;
 
@@ -108,36 +108,59 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
             atomicExch(status, (int)PW_ERR_TIMEOUT);
         }
     };
-    // in-place conversion of a landed plane: doubles -> (hi, hi, lo, lo) chunks
+    // in-place conversion of a landed plane: doubles -> (hi, hi, lo, lo) chunks.
+    // Thread (tk, tj) converts chunk tk+1 of rows tj, tj+TJ, ... of the
+    // 3*(TJ+2) rows (u, v, w); the first 6*(TJ+2) threads also convert one of
+    // the two edge chunks (k halo) of a row.
+    constexpr int ROWS = 3 * (TJ + 2);
+    auto conv_chunk = [&](double *base, int R, int q) {
+        const int f = R / (TJ + 2), r = R - f * (TJ + 2);
+        double *cp = base + (size_t)f * fs + (size_t)r * g.kb + 2 * q;
+        uint4 d = *reinterpret_cast<const uint4 *>(cp);  // (lo, hi) words of two doubles
+        const int klev = k0 - 2 + 2 * q;
+        const int kz = (f == 2) ? g.nz - 1 : g.nz;
+        if (klev >= kz) d.x = d.y = 0u;
+        if (klev + 1 >= kz) d.z = d.w = 0u;
+        float h0, l0, h1, l1;
+        split_words(d.x, d.y, h0, l0);
+        split_words(d.z, d.w, h1, l1);
+        *reinterpret_cast<float4 *>(cp) = make_float4(h0, h1, l0, l1);
+    };
     auto convert = [&](int p) {
         double *base = planes + (size_t)(p % NS) * 3 * fs;
-        const int total = g.rows * g.cpr, rpf = g.tj + 2;
-        for (int c = tid; c < total; c += nt) {
-            const int row = (int)(((float)c + 0.5f) * g.inv_cpr);
-            const int q = c - row * g.cpr;
-            const int f = (row >= rpf) + (row >= 2 * rpf);
-            const int r = row - f * rpf;
-            double *cp = base + (size_t)f * fs + (size_t)r * g.kb + 2 * q;
-            double2 d = *reinterpret_cast<const double2 *>(cp);
-            const int klev = k0 - 2 + 2 * q;
-            const int kz = (f == 2) ? g.nz - 1 : g.nz;
-            if (klev >= kz) d.x = 0.0;
-            if (klev + 1 >= kz) d.y = 0.0;
-            float h0, l0, h1, l1;
-            split_double(d.x, h0, l0);
-            split_double(d.y, h1, l1);
-            *reinterpret_cast<float4 *>(cp) = make_float4(h0, h1, l0, l1);
+#pragma unroll
+        for (int m = 0; m < (ROWS + TJ - 1) / TJ; m++) {
+            const int R = tj + m * TJ;
+            if (R < ROWS) conv_chunk(base, R, tk + 1);
         }
+        for (int e = tid; e < 2 * ROWS; e += nt) conv_chunk(base, e >> 1, (e & 1) ? nkt + 1 : 0);
     };
 
-    // per-thread coefficients for levels (k, k+1) and their shifts
-    const int N = g.cs_n;
-    const int kq = min(kbase, g.nz - 1);  // threads past the top only read valid entries
-    const D2 Gm = cs_pair(cs, N, 0, kq - 1), G0 = cs_pair(cs, N, 0, kq);
-    const D2 GP0 = cs_pair(cs, N, 1, kq), GPp = cs_pair(cs, N, 1, kq + 1);
-    const D2 R0 = cs_pair(cs, N, 2, kq), RP0 = cs_pair(cs, N, 3, kq);
-    const float *tc = cs + 8 * N;
-    const D2 TCX{pk(tc[0], tc[0]), pk(tc[1], tc[1])}, TCY{pk(tc[2], tc[2]), pk(tc[3], tc[3])};
+    // coefficients of each level pair of the chunk, prepared once per CTA in
+    // shared memory (keeps them out of the register file during the march):
+    // per pair t: Gm, G0, GP0, GPp, R0, RP0 as float4 (hi pair, lo pair)
+    float4 *ctab = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(bars) + 64);
+    for (int t = tid; t < nkt; t += nt) {
+        const int N = g.cs_n;
+        const int kq = min(k0 + 2 * t, g.nz - 1);  // pairs past the top read valid entries
+        const D2 c6[6] = {cs_pair(cs, N, 0, kq - 1), cs_pair(cs, N, 0, kq), cs_pair(cs, N, 1, kq),
+                          cs_pair(cs, N, 1, kq + 1), cs_pair(cs, N, 2, kq), cs_pair(cs, N, 3, kq)};
+        for (int a = 0; a < 6; a++)
+            ctab[t * 6 + a] = make_float4(lx(c6[a].h), ly(c6[a].h), lx(c6[a].l), ly(c6[a].l));
+    }
+    if (tid == 0) {
+        const float *tc = cs + 8 * g.cs_n;
+        ctab[nkt * 6] = make_float4(tc[0], tc[0], tc[1], tc[1]);
+        ctab[nkt * 6 + 1] = make_float4(tc[2], tc[2], tc[3], tc[3]);
+    }
+    auto coef = [&](int a) {
+        const float4 c = ctab[tk * 6 + a];
+        return D2{pk(c.x, c.y), pk(c.z, c.w)};
+    };
+    auto tcoef = [&](int a) {
+        const float4 c = ctab[nkt * 6 + a];
+        return D2{pk(c.x, c.y), pk(c.z, c.w)};
+    };
     const bool active = (j < g.ny) && (kbase < g.nz);
 
     // planes i0-1 and i0
@@ -152,8 +175,16 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
             return;
         }
     }
+    // x face sums of column i0-1|i0, carried along the march
     D2 Fx_m, Gx_m, Hx_m;
-    bool first = true;
+    {
+        const double *Pm = planes, *Pc = planes + 3 * fs;  // planes 0 and 1 (slots 0, 1)
+        const int rC = (tj + 1) * g.kb, rN = (tj + 2) * g.kb;
+        const D2 uM0 = ld2<0>(Pm + rC, kk), uC0 = ld2<0>(Pc + rC, kk);
+        Fx_m = df_add(uM0, uC0);
+        Gx_m = df_add(uM0, ld2<0>(Pm + rN, kk));
+        Hx_m = df_add(uM0, ld2<1>(Pm + rC, kk));
+    }
     for (int i = i0; i < i_end; i++) {
         const int q = i - i0 + 1;
         bool ok = wait(q + 1);
@@ -178,49 +209,45 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
 
         // ---------------- su ----------------
         const D2 uM0 = ld2<0>(uM, kk), uC0 = ld2<0>(uC, kk), uP0 = ld2<0>(uP, kk);
-        if (first) Fx_m = df_add(uM0, uC0);
         const D2 Fx_p = df_add(uC0, uP0);
-        D2 X = df_mul(df_sub(df_mul(uM0, Fx_m), df_mul(uP0, Fx_p)), TCX);
+        D2 X = df_mul(df_sub(df_mul(uM0, Fx_m), df_mul(uP0, Fx_p)), tcoef(0));
         const D2 uS0 = ld2<0>(Pc + rS, kk), uN0 = ld2<0>(Pc + rN, kk);
         const D2 vS0 = ld2<0>(Pc + fs + rS, kk), vSP0 = ld2<0>(Pp + fs + rS, kk);
         const D2 vC0 = ld2<0>(vCr, kk), vP0 = ld2<0>(vPr, kk);
-        D2 Y = df_mul(df_sub(df_mul(uS0, df_add(vS0, vSP0)), df_mul(uN0, df_add(vC0, vP0))), TCY);
+        D2 Y = df_mul(df_sub(df_mul(uS0, df_add(vS0, vSP0)), df_mul(uN0, df_add(vC0, vP0))), tcoef(1));
         const D2 wCm = ld2<-1>(wCr, kk), wPm = ld2<-1>(wPr, kk);
         const D2 wC0 = ld2<0>(wCr, kk), wP0 = ld2<0>(wPr, kk);
         const D2 uCm = ld2<-1>(uC, kk), uCp = ld2<1>(uC, kk);
-        D2 Z = df_mul(df_sub(df_mul(uCm, df_mul(df_add(wCm, wPm), Gm)),
-                             df_mul(uCp, df_mul(df_add(wC0, wP0), G0))), R0);
+        D2 Z = df_mul(df_sub(df_mul(uCm, df_mul(df_add(wCm, wPm), coef(0))),
+                             df_mul(uCp, df_mul(df_add(wC0, wP0), coef(1)))), coef(4));
         const D2 ru = df_add(df_add(X, Y), Z);
 
         // ---------------- sv ----------------
         const D2 vM0 = ld2<0>(vMr, kk), uNM0 = ld2<0>(Pm + rN, kk);
-        if (first) Gx_m = df_add(uM0, uNM0);
         const D2 Gx_p = df_add(uC0, uN0);
-        X = df_mul(df_sub(df_mul(vM0, Gx_m), df_mul(vP0, Gx_p)), TCX);
+        X = df_mul(df_sub(df_mul(vM0, Gx_m), df_mul(vP0, Gx_p)), tcoef(0));
         const D2 vN0 = ld2<0>(Pc + fs + rN, kk);
-        Y = df_mul(df_sub(df_mul(vS0, df_add(vS0, vC0)), df_mul(vN0, df_add(vC0, vN0))), TCY);
+        Y = df_mul(df_sub(df_mul(vS0, df_add(vS0, vC0)), df_mul(vN0, df_add(vC0, vN0))), tcoef(1));
         const D2 wNm = ld2<-1>(Pc + 2 * fs + rN, kk), wN0 = ld2<0>(Pc + 2 * fs + rN, kk);
         const D2 vCm = ld2<-1>(vCr, kk), vCp = ld2<1>(vCr, kk);
-        Z = df_mul(df_sub(df_mul(vCm, df_mul(df_add(wCm, wNm), Gm)),
-                          df_mul(vCp, df_mul(df_add(wC0, wN0), G0))), R0);
+        Z = df_mul(df_sub(df_mul(vCm, df_mul(df_add(wCm, wNm), coef(0))),
+                          df_mul(vCp, df_mul(df_add(wC0, wN0), coef(1)))), coef(4));
         const D2 rv = df_add(df_add(X, Y), Z);
 
         // ---------------- sw ----------------
         const D2 wM0 = ld2<0>(wMr, kk), uMp = ld2<1>(uM, kk);
-        if (first) Hx_m = df_add(uM0, uMp);
         const D2 Hx_p = df_add(uC0, uCp);
-        X = df_mul(df_sub(df_mul(wM0, Hx_m), df_mul(wP0, Hx_p)), TCX);
+        X = df_mul(df_sub(df_mul(wM0, Hx_m), df_mul(wP0, Hx_p)), tcoef(0));
         const D2 wS0 = ld2<0>(Pc + 2 * fs + rS, kk), vSp = ld2<1>(Pc + fs + rS, kk);
-        Y = df_mul(df_sub(df_mul(wS0, df_add(vS0, vSp)), df_mul(wN0, df_add(vC0, vCp))), TCY);
+        Y = df_mul(df_sub(df_mul(wS0, df_add(vS0, vSp)), df_mul(wN0, df_add(vC0, vCp))), tcoef(1));
         const D2 wCp = ld2<1>(wCr, kk);
-        Z = df_mul(df_sub(df_mul(wCm, df_mul(df_add(wCm, wC0), GP0)),
-                          df_mul(wCp, df_mul(df_add(wC0, wCp), GPp))), RP0);
+        Z = df_mul(df_sub(df_mul(wCm, df_mul(df_add(wCm, wC0), coef(2))),
+                          df_mul(wCp, df_mul(df_add(wC0, wCp), coef(3)))), coef(5));
         const D2 rw = df_add(df_add(X, Y), Z);
 
         Fx_m = Fx_p;
         Gx_m = Gx_p;
         Hx_m = Hx_p;
-        first = false;
 
         // ---------------- outputs ----------------
         const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
@@ -233,7 +260,7 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
             double2 *pu = reinterpret_cast<double2 *>(su + off);
             double2 *pv = reinterpret_cast<double2 *>(sv + off);
             double2 *pw = reinterpret_cast<double2 *>(sw + off);
-            if (beta) {
+            if (BETA) {
                 const double2 ou = *pu, ov = *pv, ow = *pw;
                 a0 += ou.x; a1 += ou.y; b0 += ov.x; b1 += ov.y; c0 += ow.x; c1 += ow.y;
             }
@@ -241,9 +268,9 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
             *pv = make_double2(b0, b1);
             *pw = make_double2(c0, c1);
         } else {
-            su[off] = beta ? su[off] + a0 : a0;
-            sv[off] = beta ? sv[off] + b0 : b0;
-            sw[off] = beta ? sw[off] + c0 : c0;
+            su[off] = BETA ? su[off] + a0 : a0;
+            sv[off] = BETA ? sv[off] + b0 : b0;
+            sw[off] = BETA ? sw[off] + c0 : c0;
         }
     }
 }
@@ -252,6 +279,8 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
                                  void *su, void *sv, void *sw, int beta, cudaStream_t st,
                                  int tile_j, int tile_i) {
     constexpr int NS = 5;
+    constexpr int TJ = 8;  // the split kernel is compiled for 8 rows of columns per CTA
+    tile_j = TJ;
     PwSplitGeom g;
     g.nx = m->nx;
     g.ny = m->ny;
@@ -272,7 +301,9 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
     const int threads = (g.kc / 2) * tile_j;
     if (threads > 256)
         return pw_fail(PW_ERR_SHAPE, "split kernel: tile_j=%d needs %d threads (max 256)", tile_j, threads);
-    const size_t smem = (size_t)NS * 3 * g.field_stride * 8 + NS * sizeof(uint64_t);
+    static_assert(NS * sizeof(uint64_t) <= 64, "barrier slot");
+    const size_t smem = (size_t)NS * 3 * g.field_stride * 8 + 64 +
+                        ((size_t)(g.kc / 2) * 6 + 2) * sizeof(float4);
     if (smem > 227 * 1024) return pw_fail(PW_ERR_SHAPE, "split kernel needs %zu bytes of shared memory", smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
@@ -280,13 +311,13 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
         pw_status s = pw_make_field_map(&maps[q], f[q], PW_F64, m->nx, m->ny, m->nzp, g.kb, tile_j + 2);
         if (s != PW_OK) return s;
     }
-    auto kern = pw_advect_split_kernel<NS>;
+    auto kern = beta ? pw_advect_split_kernel<NS, TJ, true> : pw_advect_split_kernel<NS, TJ, false>;
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)((m->nz + g.kc - 1) / g.kc));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");
     kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (double *)su, (double *)sv, (double *)sw,
-                                      m->coefsplit, g, beta, m->status);
+                                      m->coefsplit, g, m->status);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
 }

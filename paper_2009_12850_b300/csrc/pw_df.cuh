@@ -93,12 +93,12 @@ __device__ __forceinline__ D2 df_mul(D2 a, D2 b) {
 // ---------------------------------------------------------------------------
 // conversions
 // ---------------------------------------------------------------------------
-// Split a double into (hi, lo): hi = x truncated to 24 significant bits, lo =
-// the next 23 bits (exact float subtraction of the implicit bit), so
-// |x - hi - lo| < 2^-46 |x|.  Integer operations only.  Values with
-// |x| < 2^-100 (and zeros) give (0, 0); |x| must be below 2^127.
-__device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
-    const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+// Split a double, given as its two 32-bit words, into (hi, lo): hi = x
+// truncated to 24 significant bits, lo = the next 23 bits (an exact float
+// subtraction removes the implicit bit), so |x - hi - lo| < 2^-46 |x|.
+// Integer operations plus one FP32 subtraction.  Values with |x| < 2^-100
+// (and zeros) give (0, 0); |x| must be below 2^127.
+__device__ __forceinline__ void split_words(uint32_t xl, uint32_t xh, float &hi, float &lo) {
     // top 23 mantissa bits and the low 8 exponent bits, then rebias 1023 -> 127
     const uint32_t f = __funnelshift_l(xl, xh, 3) ^ 0x40000000u;
     const uint32_t hb = (f & 0x7fffffffu) | (xh & 0x80000000u);

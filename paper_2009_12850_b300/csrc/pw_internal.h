@@ -119,14 +119,16 @@ __device__ __forceinline__ void pw_mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware (up to
+// ~0.1 ms per call) instead of spinning on the issue slots.
 __device__ __forceinline__ bool pw_mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(pw_smem_u32(bar)), "r"(parity)
+        : "r"(pw_smem_u32(bar)), "r"(parity), "r"(100000u)
         : "memory");
     return ok != 0;
 }
