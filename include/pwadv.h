@@ -142,6 +142,12 @@ pw_status pw_mesh_get_tile(const pw_mesh *mesh, int *tile_j, int *tile_i);
  * f1 must be non-NULL; f2, f3 may be NULL. */
 pw_status pw_halo_periodic(const pw_mesh *mesh, void *f1, void *f2, void *f3, void *stream);
 
+/* Adjoint of pw_halo_periodic: each halo value of up to three fields is ADDED
+ * onto the interior value it is a periodic copy of, and the halo is set to 0.
+ * Used to fold gradients that reached halo entries back onto the interior
+ * degrees of freedom.  FP32 and FP64 meshes.  f2, f3 may be NULL. */
+pw_status pw_halo_fold(const pw_mesh *mesh, void *f1, void *f2, void *f3, void *stream);
+
 /* PW advection source terms (section 3.1): with halos of u, v, w filled,
  *  su = tcx [u(i-1)(u(i-1)+u(i)) - u(i+1)(u(i)+u(i+1))]
  *     + tcy [u(j-1)(v(i,j-1)+v(i+1,j-1)) - u(j+1)(v(i,j)+v(i+1,j))]
@@ -214,9 +220,9 @@ pw_status pw_check_lid(const pw_mesh *mesh, const void *w, void *stream);
  * advected in ONE persistent launch.
  * -------------------------------------------------------------------------*/
 
-/* Create a batch over n meshes (all PW_F32, or all PW_F64 / PW_BF16); the
- * meshes must outlive the batch.  Device tables are built on `stream` and the
- * call synchronises it. */
+/* Create a batch over n PW_F32 meshes (each its own nx, ny, nz, dx, dy, dz);
+ * the meshes must outlive the batch.  Device tables are built on `stream` and
+ * the call synchronises it. */
 pw_status pw_batch_create(pw_mesh *const *meshes, int n, void *stream, pw_batch **out);
 void pw_batch_destroy(pw_batch *batch);
 
@@ -234,6 +240,10 @@ pw_status pw_advect_batched(pw_batch *batch, int beta, void *stream);
 
 /* Periodic halo fill of the bound u, v, w of every member in one launch. */
 pw_status pw_batch_halo(pw_batch *batch, void *stream);
+
+/* Read (and with clear != 0 reset) the batch's device status word (0 or
+ * PW_ERR_TIMEOUT; sticky like the mesh status).  Synchronises `stream`. */
+pw_status pw_batch_status(pw_batch *batch, int clear, void *stream, int *status);
 
 /* ---------------------------------------------------------------------------
  * Tile autotuner (tile shapes chosen by timing candidates on the device).

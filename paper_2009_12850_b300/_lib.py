@@ -54,6 +54,7 @@ _SIGS = {
     "pw_mesh_set_tile": ([_vp, _i, _i], _i),
     "pw_mesh_get_tile": ([_vp, _ip, _ip], _i),
     "pw_halo_periodic": ([_vp, _vp, _vp, _vp, _vp], _i),
+    "pw_halo_fold": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_advect": ([_vp] + [_vp] * 6 + [_i, _vp], _i),
     "pw_advect_adjoint": ([_vp] + [_vp] * 9 + [_d, _i, _vp], _i),
     "pw_euler_adjoint": ([_vp] + [_vp] * 9 + [_d, _vp], _i),
@@ -65,6 +66,7 @@ _SIGS = {
     "pw_batch_set_fields": ([_vp] + [ctypes.POINTER(_vp)] * 6 + [_vp], _i),
     "pw_advect_batched": ([_vp, _i, _vp], _i),
     "pw_batch_halo": ([_vp, _vp], _i),
+    "pw_batch_status": ([_vp, _i, _vp, _ip], _i),
     "pw_autotune": ([_vp] + [_vp] * 6 + [ctypes.c_char_p, _vp, _fp], _i),
     "pw_batch_autotune": ([_vp, ctypes.c_char_p, _vp, _fp], _i),
     "pw_status_string": ([_i], ctypes.c_char_p),
@@ -144,6 +146,10 @@ def pw_halo_periodic(mesh, f1, f2, f3, stream):
     check(_c.pw_halo_periodic(mesh, f1, f2, f3, stream), "pw_halo_periodic")
 
 
+def pw_halo_fold(mesh, f1, f2, f3, stream):
+    check(_c.pw_halo_fold(mesh, f1, f2, f3, stream), "pw_halo_fold")
+
+
 def pw_advect(mesh, u, v, w, su, sv, sw, beta, stream):
     check(_c.pw_advect(mesh, u, v, w, su, sv, sw, int(beta), stream), "pw_advect")
 
@@ -200,6 +206,12 @@ def pw_advect_batched(batch, beta, stream):
 
 def pw_batch_halo(batch, stream):
     check(_c.pw_batch_halo(batch, stream), "pw_batch_halo")
+
+
+def pw_batch_status(batch, clear, stream):
+    st = ctypes.c_int()
+    check(_c.pw_batch_status(batch, int(clear), stream, ctypes.byref(st)), "pw_batch_status")
+    return st.value
 
 
 def pw_autotune(mesh, u, v, w, su, sv, sw, cache_path, stream):

@@ -115,6 +115,10 @@ class Mesh:
         ps = [self._check(f1, "f1")] + [self._check(f, "f") if f is not None else None for f in (f2, f3)]
         L.pw_halo_periodic(self.handle, ps[0], ps[1], ps[2], _stream(stream))
 
+    def halo_fold(self, f1, f2=None, f3=None, stream=None):
+        ps = [self._check(f1, "f1")] + [self._check(f, "f") if f is not None else None for f in (f2, f3)]
+        L.pw_halo_fold(self.handle, ps[0], ps[1], ps[2], _stream(stream))
+
     def advect(self, u, v, w, su=None, sv=None, sw=None, beta=0, stream=None):
         su = self.empty_out() if su is None else su
         sv = self.empty_out() if sv is None else sv
@@ -177,3 +181,45 @@ class Mesh:
         return L.pw_autotune(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
                              self._check(su, "su", True), self._check(sv, "sv", True),
                              self._check(sw, "sw", True), cache_path, _stream(stream))
+
+
+class Batch:
+    """Many independent FP32 meshes advected in one persistent launch."""
+
+    def __init__(self, meshes, stream=None):
+        self.meshes = list(meshes)
+        self.handle = L.pw_batch_create([m.handle for m in self.meshes], _stream(stream))
+        self.fields = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.pw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bind(self, fields, sources, stream=None):
+        """fields: list of (u, v, w) per member; sources: list of (su, sv, sw)."""
+        cols = [[], [], [], [], [], []]
+        for m, f, s in zip(self.meshes, fields, sources):
+            for q in range(3):
+                cols[q].append(m._check(f[q], "uvw"[q]))
+                cols[3 + q].append(m._check(s[q], "s" + "uvw"[q], True))
+        L.pw_batch_set_fields(self.handle, *cols, _stream(stream))
+        self.fields, self.sources = fields, sources
+
+    def halo(self, stream=None):
+        L.pw_batch_halo(self.handle, _stream(stream))
+
+    def advect(self, beta=0, stream=None):
+        L.pw_advect_batched(self.handle, beta, _stream(stream))
+
+    def autotune(self, cache_path=None, stream=None):
+        return L.pw_batch_autotune(self.handle, cache_path, _stream(stream))
+
+    def status(self, clear=True, stream=None):
+        return L.pw_batch_status(self.handle, clear, _stream(stream))

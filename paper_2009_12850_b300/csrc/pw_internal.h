@@ -28,34 +28,6 @@ struct pw_mesh {
     int tile_j, tile_i;      // stencil tile: rows per CTA, columns marched per CTA
 };
 
-// one member of a batch as the persistent kernel sees it
-struct PwMember {
-    const void *u, *v, *w;
-    void *su, *sv, *sw;
-    const float *coef;       // tzc1 tzc2 tzd1 tzd2, 4*nz
-    int nx, ny, nz, nzp;
-    float tcx, tcy;
-    int tile_j, tile_i;      // tile shape for this member
-    int tiles_j, tiles_i;    // tile counts
-    int first_tile;          // prefix sum over members
-    int pad_;
-};
-
-struct pw_batch {
-    int n;
-    pw_mesh **meshes;
-    PwMember *host_members;
-    PwMember *dev_members;
-    int *counter;            // device work counter
-    int *status;
-    int total_tiles;
-    int grid;                // persistent CTAs
-    int max_threads;         // largest CTA any member needs
-    size_t smem;             // dynamic shared memory of the launch
-    int bound;               // fields bound
-    pw_dtype dtype;
-};
-
 // reduction geometry of pw_residuals (fixed so the order of sums is fixed)
 #define PW_RED_BLOCKS 592
 #define PW_RED_THREADS 256
@@ -106,6 +78,10 @@ __device__ __forceinline__ uint32_t pw_smem_u32(const void *p) {
 __device__ __forceinline__ void pw_mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(pw_smem_u32(bar)), "r"(count)
                  : "memory");
+}
+
+__device__ __forceinline__ void pw_mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(pw_smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void pw_fence_barrier_init() {

@@ -1,0 +1,282 @@
+// pw_march.cuh -- the x-march over TMA-staged (j,k) planes, shared by the
+// single-mesh stencil kernel (pw_advect.cu) and the persistent batched kernel
+// (pw_batch.cu).
+//
+// Each thread owns KV consecutive levels of one column and a warp covers a
+// whole column segment with 16-byte accesses.  A CTA tile is tile_j rows of
+// columns (y) and one k chunk, marched along x: a ring of ns (j,k) planes of
+// u, v, w lives in shared memory, each holding tile_j + 2 rows (the y halo)
+// and the k chunk plus a 16-byte k halo on each side.  Planes are fetched by
+// TMA (one elected thread, completion on an mbarrier) ns - 3 planes ahead of
+// the one being consumed, so every value of u, v, w is read from HBM once per
+// tile (plus the y halo and the two priming planes).  Each step computes su,
+// sv, sw for plane i from planes i-1, i, i+1 and stores them with 16-byte
+// stores.
+#pragma once
+
+#include <type_traits>
+
+#include "pw_internal.h"
+
+struct PwGeom {
+    int nx, ny, nz, nzp;
+    int kc;            // k chunk per CTA (multiple of KV and of the k halo)
+    int kb;            // TMA box k extent = kc + 2*h
+    int h;             // k halo in elements (16 bytes)
+    int tj, ti;        // rows per CTA, columns marched per CTA
+    int ns;            // planes in the ring
+    int field_stride;  // elements between the u, v, w planes of one slot
+    int plane_elems;   // (tj + 2) * kb
+    long long si, sj;  // strides of the sources (elements)
+    double tcx, tcy;
+};
+
+// --------------------------------------------------------------------------
+// slab loads from shared memory: KV values at [kk, kk+KV) plus optional
+// neighbours kk-1 and kk+KV, widened to the compute type
+// --------------------------------------------------------------------------
+template <typename TS, typename TC, int KV>
+struct SlabLoad;
+
+template <typename TC>
+struct SlabLoad<float, TC, 4> {
+    static __device__ __forceinline__ void run(const float *p, TC *o) {
+        float4 a = *reinterpret_cast<const float4 *>(p);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    }
+};
+template <typename TC>
+struct SlabLoad<double, TC, 2> {
+    static __device__ __forceinline__ void run(const double *p, TC *o) {
+        double2 a = *reinterpret_cast<const double2 *>(p);
+        o[0] = a.x; o[1] = a.y;
+    }
+};
+template <typename TC>
+struct SlabLoad<double, TC, 4> {
+    static __device__ __forceinline__ void run(const double *p, TC *o) {
+        double2 a = *reinterpret_cast<const double2 *>(p);
+        double2 b = *reinterpret_cast<const double2 *>(p + 2);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+};
+template <typename TC>
+struct SlabLoad<__nv_bfloat16, TC, 4> {
+    static __device__ __forceinline__ void run(const __nv_bfloat16 *p, TC *o) {
+        uint2 a = *reinterpret_cast<const uint2 *>(p);
+        // bf16 -> f32 is exact: the bf16 bits are the top half of the f32
+        o[0] = __uint_as_float(a.x << 16);
+        o[1] = __uint_as_float(a.x & 0xffff0000u);
+        o[2] = __uint_as_float(a.y << 16);
+        o[3] = __uint_as_float(a.y & 0xffff0000u);
+    }
+};
+
+// x[0] = value at k-1, x[1..KV] = k..k+KV-1, x[KV+1] = k+KV
+template <typename TS, typename TC, int KV, bool LO, bool HI>
+__device__ __forceinline__ void pw_col(const TS *row, int kk, TC (&x)[KV + 2]) {
+    SlabLoad<TS, TC, KV>::run(row + kk, x + 1);
+    x[0] = LO ? pw_to<TC>(row[kk - 1]) : TC(0);
+    x[KV + 1] = HI ? pw_to<TC>(row[kk + KV]) : TC(0);
+}
+
+// --------------------------------------------------------------------------
+// vector stores of KV results (with optional accumulate), masked at the top
+// --------------------------------------------------------------------------
+template <typename TO, int KV>
+__device__ __forceinline__ void pw_store(TO *p, const TO (&r)[KV], int nvalid, int beta) {
+    if (nvalid >= KV) {
+        if constexpr (sizeof(TO) * KV == 16) {
+            using V = typename std::conditional<sizeof(TO) == 8, double2, float4>::type;
+            V val;
+            TO *vv = reinterpret_cast<TO *>(&val);
+            if (beta) {
+                V old = *reinterpret_cast<const V *>(p);
+                const TO *oo = reinterpret_cast<const TO *>(&old);
+#pragma unroll
+                for (int m = 0; m < KV; m++) vv[m] = oo[m] + r[m];
+            } else {
+#pragma unroll
+                for (int m = 0; m < KV; m++) vv[m] = r[m];
+            }
+            *reinterpret_cast<V *>(p) = val;
+        } else {
+#pragma unroll
+            for (int m = 0; m < KV; m++) p[m] = beta ? p[m] + r[m] : r[m];
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < KV; m++)
+            if (m < nvalid) p[m] = beta ? p[m] + r[m] : r[m];
+    }
+}
+
+// --------------------------------------------------------------------------
+// one tile of the x-march: tile_j rows from j0, columns i0 .. i0+tile_i-1, the
+// k chunk starting at k0.  Shared memory: ns plane slots then ns mbarriers
+// (initialised here, invalidated before returning so the caller may run the
+// next tile).  Returns false if a TMA wait timed out (status recorded).
+// --------------------------------------------------------------------------
+template <typename TS, typename TC, typename TO, int KV>
+__device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUtensorMap *mv_,
+                                              const CUtensorMap *mw_, TO *__restrict__ su,
+                                              TO *__restrict__ sv, TO *__restrict__ sw,
+                                              const TC *__restrict__ coef, const PwGeom &g, int beta,
+                                              int *__restrict__ status, unsigned char *smem_raw,
+                                              int j0, int i0, int k0) {
+    const CUtensorMap &mu = *mu_, &mv = *mv_, &mw = *mw_;
+    TS *planes = reinterpret_cast<TS *>(smem_raw);
+    uint64_t *bars =
+        reinterpret_cast<uint64_t *>(smem_raw + (size_t)g.ns * 3 * g.field_stride * sizeof(TS));
+
+    const int nkt = g.kc / KV;
+    const int tk = threadIdx.x % nkt, tj = threadIdx.x / nkt;
+    const int i_end = min(i0 + g.ti, g.nx);
+    const int nplanes = i_end - i0 + 2;  // planes i0-1 .. i_end
+    const uint32_t plane_bytes = 3u * (uint32_t)g.plane_elems * (uint32_t)sizeof(TS);
+    const int kbase = k0 + tk * KV;      // first level of this thread
+    const int kk = g.h + tk * KV;        // its position inside a plane row
+    const int j = j0 + tj;
+
+    if (threadIdx.x == 0) {
+        pw_prefetch_map(&mu);
+        pw_prefetch_map(&mv);
+        pw_prefetch_map(&mw);
+        for (int s = 0; s < g.ns; s++) pw_mbar_init(&bars[s], 1);
+        pw_fence_barrier_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int p) {
+        int s = p % g.ns;
+        TS *dst = planes + (size_t)s * 3 * g.field_stride;
+        pw_mbar_expect_tx(&bars[s], plane_bytes);
+        int c0 = k0 - g.h, c1 = j0 + 1, c2 = i0 + 1 + p;  // (k, j-1, i-1+p) + halo offset
+        pw_tma_load_3d(dst, &mu, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + g.field_stride, &mv, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + 2 * g.field_stride, &mw, c0, c1, c2, &bars[s]);
+    };
+    int issued = 0;  // planes handed to TMA (thread 0's count)
+    if (threadIdx.x == 0) {
+        for (int p = 0; p < min(g.ns, nplanes); p++) issue(p);
+        issued = min(g.ns, nplanes);
+    }
+
+    // vertical coefficients of this thread's levels (0 beyond nz)
+    TC c1[KV], c2[KV], d1[KV], d2[KV];
+#pragma unroll
+    for (int m = 0; m < KV; m++) {
+        int k = kbase + m;
+        bool in = k < g.nz;
+        c1[m] = in ? coef[k] : TC(0);
+        c2[m] = in ? coef[g.nz + k] : TC(0);
+        d1[m] = in ? coef[2 * g.nz + k] : TC(0);
+        d2[m] = in ? coef[3 * g.nz + k] : TC(0);
+    }
+    const TC tcx = (TC)g.tcx, tcy = (TC)g.tcy;
+    const bool active = (tj < g.tj) && (j < g.ny) && (kbase < g.nz);
+    const bool top = kbase + KV >= g.nz - 1;  // slab touches the lid or the padding
+    const int nvalid = g.nz - kbase;
+    const int row_len = g.kb;
+
+    int waited = 0;
+    for (int i = i0; i < i_end; i++) {
+        const int q = i - i0 + 1;  // plane index of column i
+        bool ok = true;
+        while (waited <= q + 1 && ok) {
+            ok = pw_mbar_wait_bounded(&bars[waited % g.ns], (uint32_t)((waited / g.ns) & 1));
+            if (ok) waited++;
+        }
+        if (!__syncthreads_and(ok)) {
+            // give up: wait (bounded) for copies still in flight, record, leave
+            if (threadIdx.x == 0) {
+                for (int p = waited; p < issued; p++)
+                    if (!pw_mbar_wait_bounded(&bars[p % g.ns], (uint32_t)((p / g.ns) & 1),
+                                              PW_DRAIN_CYCLES))
+                        break;
+                atomicExch(status, (int)PW_ERR_TIMEOUT);
+            }
+            return false;
+        }
+        // everyone is past step i-1: the slot of plane q-2 is free
+        if (threadIdx.x == 0 && q >= 2 && q - 2 + g.ns < nplanes) {
+            issue(q - 2 + g.ns);
+            issued = q - 1 + g.ns;
+        }
+        if (!active) continue;
+
+        const TS *Pm = planes + (size_t)((q - 1) % g.ns) * 3 * g.field_stride;
+        const TS *Pc = planes + (size_t)(q % g.ns) * 3 * g.field_stride;
+        const TS *Pp = planes + (size_t)((q + 1) % g.ns) * 3 * g.field_stride;
+        const int fs = g.field_stride;
+        const int rS = tj * row_len, rC = (tj + 1) * row_len, rN = (tj + 2) * row_len;
+
+        TC uC[KV + 2], uM[KV + 2], uP[KV + 2], vC[KV + 2], vM[KV + 2], vP[KV + 2];
+        TC wC[KV + 2], wM[KV + 2], wP[KV + 2];
+        TC uS[KV + 2], vS[KV + 2], vSP[KV + 2], wS[KV + 2];
+        TC uN[KV + 2], uNM[KV + 2], vN[KV + 2], wN[KV + 2];
+        pw_col<TS, TC, KV, true, true>(Pc + rC, kk, uC);
+        pw_col<TS, TC, KV, false, true>(Pm + rC, kk, uM);
+        pw_col<TS, TC, KV, false, false>(Pp + rC, kk, uP);
+        pw_col<TS, TC, KV, true, true>(Pc + fs + rC, kk, vC);
+        pw_col<TS, TC, KV, false, false>(Pm + fs + rC, kk, vM);
+        pw_col<TS, TC, KV, false, false>(Pp + fs + rC, kk, vP);
+        pw_col<TS, TC, KV, true, true>(Pc + 2 * fs + rC, kk, wC);
+        pw_col<TS, TC, KV, false, false>(Pm + 2 * fs + rC, kk, wM);
+        pw_col<TS, TC, KV, true, false>(Pp + 2 * fs + rC, kk, wP);
+        pw_col<TS, TC, KV, false, false>(Pc + rS, kk, uS);
+        pw_col<TS, TC, KV, false, true>(Pc + fs + rS, kk, vS);
+        pw_col<TS, TC, KV, false, false>(Pp + fs + rS, kk, vSP);
+        pw_col<TS, TC, KV, false, false>(Pc + 2 * fs + rS, kk, wS);
+        pw_col<TS, TC, KV, false, false>(Pc + rN, kk, uN);
+        pw_col<TS, TC, KV, false, false>(Pm + rN, kk, uNM);
+        pw_col<TS, TC, KV, false, false>(Pc + fs + rN, kk, vN);
+        pw_col<TS, TC, KV, true, false>(Pc + 2 * fs + rN, kk, wN);
+
+        if (top) {
+            // levels >= nz are padding (0); w on the lid face nz-1 is 0 by definition
+#pragma unroll
+            for (int m = 0; m < KV + 2; m++) {
+                int k = kbase - 1 + m;
+                if (k >= g.nz) {
+                    uC[m] = 0; uM[m] = 0; uP[m] = 0; vC[m] = 0; vM[m] = 0; vP[m] = 0;
+                    uS[m] = 0; vS[m] = 0; vSP[m] = 0; uN[m] = 0; uNM[m] = 0; vN[m] = 0;
+                }
+                if (k >= g.nz - 1) {
+                    wC[m] = 0; wM[m] = 0; wP[m] = 0; wS[m] = 0; wN[m] = 0;
+                }
+            }
+        }
+
+        TO ru[KV], rv[KV], rw[KV];
+#pragma unroll
+        for (int m = 0; m < KV; m++) {
+            const int a = m + 1;  // index of level kbase+m in the slab arrays
+            TC s;
+            s = tcx * (uM[a] * (uM[a] + uC[a]) - uP[a] * (uC[a] + uP[a]));
+            s = s + tcy * (uS[a] * (vS[a] + vSP[a]) - uN[a] * (vC[a] + vP[a]));
+            s = s + c1[m] * uC[a - 1] * (wC[a - 1] + wP[a - 1]);
+            s = s - c2[m] * uC[a + 1] * (wC[a] + wP[a]);
+            ru[m] = (TO)s;
+            s = tcx * (vM[a] * (uM[a] + uNM[a]) - vP[a] * (uC[a] + uN[a]));
+            s = s + tcy * (vS[a] * (vS[a] + vC[a]) - vN[a] * (vC[a] + vN[a]));
+            s = s + c1[m] * vC[a - 1] * (wC[a - 1] + wN[a - 1]);
+            s = s - c2[m] * vC[a + 1] * (wC[a] + wN[a]);
+            rv[m] = (TO)s;
+            s = tcx * (wM[a] * (uM[a] + uM[a + 1]) - wP[a] * (uC[a] + uC[a + 1]));
+            s = s + tcy * (wS[a] * (vS[a] + vS[a + 1]) - wN[a] * (vC[a] + vC[a + 1]));
+            s = s + d1[m] * wC[a - 1] * (wC[a - 1] + wC[a]);
+            s = s - d2[m] * wC[a + 1] * (wC[a] + wC[a + 1]);
+            rw[m] = (kbase + m < g.nz - 1) ? (TO)s : TO(0);
+        }
+        const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
+        pw_store<TO, KV>(su + off, ru, nvalid, beta);
+        pw_store<TO, KV>(sv + off, rv, nvalid, beta);
+        pw_store<TO, KV>(sw + off, rw, nvalid, beta);
+    }
+    __syncthreads();  // every thread is past its last wait: barriers can be reused
+    if (threadIdx.x == 0)
+        for (int s = 0; s < g.ns; s++) pw_mbar_inval(&bars[s]);
+    __syncthreads();
+    return true;
+}

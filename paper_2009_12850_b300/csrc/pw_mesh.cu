@@ -407,6 +407,57 @@ extern "C" pw_status pw_halo_periodic(const pw_mesh *m, void *f1, void *f2, void
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint of the periodic halo fill: every halo value is added onto the
+// interior value it copies and the halo is zeroed.  One thread per interior
+// element; it gathers from all its halo images, so there are no races.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void pw_halo_fold_kernel(T *f0, T *f1, T *f2, int nx, int ny, int nz, int nzp) {
+    T *f = blockIdx.y == 0 ? f0 : blockIdx.y == 1 ? f1 : f2;
+    int64_t n = (int64_t)nx * ny * nz;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        int k = (int)(e % nz);
+        int64_t col = e / nz;
+        int j = (int)(col % ny), i = (int)(col / ny);
+        bool ei = (i < 2) || (i >= nx - 2), ej = (j < 2) || (j >= ny - 2);
+        if (!ei && !ej) continue;
+        T acc = T(0);
+        for (int ih = i + 2 - ((i + 2) / nx) * nx; ih < nx + 4; ih += nx)
+            for (int jh = j + 2 - ((j + 2) / ny) * ny; jh < ny + 4; jh += ny) {
+                if (ih >= 2 && ih < nx + 2 && jh >= 2 && jh < ny + 2) continue;
+                T *h = f + ((int64_t)ih * (ny + 4) + jh) * nzp + k;
+                acc += *h;
+                *h = T(0);
+            }
+        f[((int64_t)(i + 2) * (ny + 4) + (j + 2)) * nzp + k] += acc;
+    }
+}
+
+extern "C" pw_status pw_halo_fold(const pw_mesh *m, void *f1, void *f2, void *f3, void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    pw_status s;
+    void *f[3] = {f1, f2, f3};
+    const char *nm[3] = {"f1", "f2", "f3"};
+    int n = 0;
+    for (int q = 0; q < 3; q++) {
+        if (q > 0 && !f[q]) continue;
+        if ((s = pw_check_ptr(f[q], nm[q])) != PW_OK) return s;
+        f[n++] = f[q];
+    }
+    if (m->dtype == PW_BF16) return pw_fail(PW_ERR_DTYPE, "pw_halo_fold supports PW_F64 and PW_F32 meshes");
+    dim3 grid((unsigned)(m->num_sms * 4), (unsigned)n);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *a = f[0], *b = n > 1 ? f[1] : f[0], *c = n > 2 ? f[2] : f[0];
+    if (m->dtype == PW_F64)
+        pw_halo_fold_kernel<double><<<grid, 256, 0, st>>>((double *)a, (double *)b, (double *)c, m->nx, m->ny, m->nz, m->nzp);
+    else
+        pw_halo_fold_kernel<float><<<grid, 256, 0, st>>>((float *)a, (float *)b, (float *)c, m->nx, m->ny, m->nz, m->nzp);
+    PW_CUDA(cudaGetLastError());
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
 // forward Euler with halo refresh: each interior element is updated once and
 // written to every halo column that is a periodic image of it.
 // ---------------------------------------------------------------------------
