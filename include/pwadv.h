@@ -211,6 +211,40 @@ pw_status pw_residuals(const pw_mesh *mesh, const void *u, const void *v, const 
                        const void *su, const void *sv, const void *sw, double *out,
                        void *stream);
 
+/* Largest nz accepted by pw_residuals_noalloc. */
+#define PW_NOALLOC_MAX_NZ 4096
+
+/* The conservation sums of pw_residuals for callers that cannot allocate
+ * device memory when they need them -- e.g. because a caching allocator holds
+ * all free device memory, or because an allocation inside a time-stepping loop
+ * could synchronise the device -- and may not even hold a mesh (creating one
+ * allocates).  The paper has no counterpart; this entry point exists for such
+ * callers only.
+ *
+ * Arguments: the interior size nx, ny, nz and padded column length nzp of the
+ * field layout (as pw_mesh_layout gives it; nzp a multiple of 8), the storage
+ * dtype, the energy weights as HOST arrays of nz doubles (w_uv = rho_n dz on
+ * u/v levels, w_w = rho_w dzn on w faces with the lid face 0; the last two
+ * columns of pw_mesh_coefficients), the DEVICE buffers u, v, w, su, sv, sw
+ * (16-byte aligned; sources binary64 for PW_F64, binary32 otherwise) and a HOST
+ * array out of 12 doubles, filled exactly as by pw_residuals.
+ *
+ * Allocation: none.  The only scratch is a file-scope device array of about
+ * 120 KB, held on every GPU that loads the library until the process exits.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  nz above PW_NOALLOC_MAX_NZ returns PW_ERR_SHAPE.  The
+ * array is shared by every call: each call rewrites all of it that it reads, so
+ * nothing depends on earlier contents, but calls that overlap on the GPU (on
+ * different streams or host threads) race on it and must be serialised by the
+ * caller.  Copies the weights in, runs the same two-pass FP64 reduction as
+ * pw_residuals on `stream`, copies out and synchronises `stream`. */
+pw_status pw_residuals_noalloc(int nx, int ny, int nz, int nzp, pw_dtype dtype,
+                               const double *w_uv, const double *w_w,
+                               const void *u, const void *v, const void *w,
+                               const void *su, const void *sv, const void *sw,
+                               double *out, void *stream);
+
 /* Return PW_ERR_LID if any lid value w(i,j,nz-1) (interior) is not 0, else
  * PW_OK.  Synchronises `stream`. */
 pw_status pw_check_lid(const pw_mesh *mesh, const void *w, void *stream);

@@ -15,6 +15,7 @@ PW_OK, PW_ERR_ARG, PW_ERR_SHAPE, PW_ERR_ALIGN, PW_ERR_DTYPE = 0, -1, -2, -3, -4
 PW_ERR_LID, PW_ERR_CUDA, PW_ERR_TIMEOUT, PW_ERR_NOMEM, PW_ERR_IO = -5, -6, -7, -8, -9
 PW_F64, PW_F32, PW_BF16 = 0, 1, 2
 PW_ALGO_AUTO, PW_ALGO_F64_NATIVE, PW_ALGO_F64_SPLIT = 0, 1, 2
+PW_NOALLOC_MAX_NZ = 4096
 
 
 class pw_mesh_desc(ctypes.Structure):
@@ -61,6 +62,7 @@ _SIGS = {
     "pw_euler": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
     "pw_residuals": ([_vp] + [_vp] * 6 + [_dp, _vp], _i),
     "pw_check_lid": ([_vp, _vp, _vp], _i),
+    "pw_residuals_noalloc": ([_i, _i, _i, _i, _i, _dp, _dp] + [_vp] * 6 + [_dp, _vp], _i),
     "pw_batch_create": ([ctypes.POINTER(_vp), _i, _vp, ctypes.POINTER(_vp)], _i),
     "pw_batch_destroy": ([_vp], None),
     "pw_batch_set_fields": ([_vp] + [ctypes.POINTER(_vp)] * 6 + [_vp], _i),
@@ -171,6 +173,16 @@ def pw_euler(mesh, u, v, w, su, sv, sw, dt, stream):
 def pw_residuals(mesh, u, v, w, su, sv, sw, stream):
     out = (ctypes.c_double * 12)()
     check(_c.pw_residuals(mesh, u, v, w, su, sv, sw, out, stream), "pw_residuals")
+    return list(out)
+
+
+def pw_residuals_noalloc(nx, ny, nz, nzp, dtype, w_uv, w_w, u, v, w, su, sv, sw, stream):
+    """Conservation sums with no device allocation (w_uv, w_w: host sequences of nz floats)."""
+    a = (ctypes.c_double * nz)(*w_uv)
+    b = (ctypes.c_double * nz)(*w_w)
+    out = (ctypes.c_double * 12)()
+    check(_c.pw_residuals_noalloc(int(nx), int(ny), int(nz), int(nzp), int(dtype), a, b, u, v, w, su, sv, sw,
+                                  out, stream), "pw_residuals_noalloc")
     return list(out)
 
 

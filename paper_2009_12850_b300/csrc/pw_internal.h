@@ -62,6 +62,10 @@ pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const
                            void *su, void *sv, void *sw, int beta, cudaStream_t st,
                            int tile_j, int tile_i);
 pw_status pw_launch_halo(const pw_mesh *m, void *const *f, int nf, cudaStream_t st);
+pw_status pw_launch_residuals_raw(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
+                                  const double *ww, const void *u, const void *v, const void *w,
+                                  const void *su, const void *sv, const void *sw, double *partials,
+                                  double *dout, cudaStream_t st);
 pw_status pw_launch_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
                               const void *su, const void *sv, const void *sw, double *partials,
                               double *dout, cudaStream_t st);

@@ -627,6 +627,26 @@ pw_status pw_launch_residuals(const pw_mesh *m, const void *u, const void *v, co
     return PW_OK;
 }
 
+// Same two passes for callers that hold the layout and the weights themselves
+// (no mesh): used by the entry point whose scratch is a static device array.
+pw_status pw_launch_residuals_raw(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
+                                  const double *ww, const void *u, const void *v, const void *w,
+                                  const void *su, const void *sv, const void *sw, double *partials,
+                                  double *dout, cudaStream_t st) {
+#define PW_RES_RAW(TF, TS)                                                                     \
+    pw_residual_pass1<TF, TS><<<PW_RED_BLOCKS, PW_RED_THREADS, 0, st>>>(                       \
+        (const TF *)u, (const TF *)v, (const TF *)w, (const TS *)su, (const TS *)sv,           \
+        (const TS *)sw, wuv, ww, nx, ny, nz, nzp, partials)
+    if (dtype == PW_F64) PW_RES_RAW(double, double);
+    else if (dtype == PW_F32) PW_RES_RAW(float, float);
+    else PW_RES_RAW(__nv_bfloat16, float);
+#undef PW_RES_RAW
+    PW_CUDA(cudaGetLastError());
+    pw_residual_pass2<<<1, PW_RED_THREADS, 0, st>>>(partials, PW_RED_BLOCKS, dout);
+    PW_CUDA(cudaGetLastError());
+    return PW_OK;
+}
+
 extern "C" pw_status pw_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
                                   const void *su, const void *sv, const void *sw, double *out,
                                   void *stream) {

@@ -1,0 +1,78 @@
+// pw_static.cu -- the conservation sums without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// diagnostics: a caching allocator (PyTorch's, or a model's own pool) may hold
+// all free device memory, so a raw cudaMalloc fails or would fragment it, and
+// inside a tight time-stepping loop an allocation can synchronise the device
+// and stall the stream.  Such a caller may also have no mesh object, since
+// creating one allocates.  pw_residuals_noalloc serves them: the caller passes
+// the field/source buffers, the layout and the energy weights (host arrays),
+// and the library uses a file-scope device array as its only scratch.
+#include <mutex>
+
+#include "pw_internal.h"
+
+// Scratch: PW_RED_BLOCKS*12 block partials, 12 final sums, then the two weight
+// columns (PW_NOALLOC_MAX_NZ doubles each).  Every GPU that loads the library
+// holds this array (about 120 KB) until the process exits.
+static __device__ __align__(256) double pw_noalloc_scratch[(PW_RED_BLOCKS + 1) * 12 + 2 * PW_NOALLOC_MAX_NZ];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_addr[256];  // device address of the array, per device ordinal
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, called once per device with that device current.
+static pw_status pw_noalloc_scratch_ptr(double **out) {
+    int dev = 0;
+    PW_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return pw_fail(PW_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, pw_noalloc_scratch);
+        if (e != cudaSuccess) return pw_cuda_fail(e, "cudaGetSymbolAddress(pw_noalloc_scratch)");
+        if (!p) return pw_fail(PW_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+        g_noalloc_addr[dev] = (double *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PW_OK;
+}
+
+extern "C" pw_status pw_residuals_noalloc(int nx, int ny, int nz, int nzp, pw_dtype dtype,
+                                          const double *w_uv, const double *w_w, const void *u,
+                                          const void *v, const void *w, const void *su, const void *sv,
+                                          const void *sw, double *out, void *stream) {
+    if (nx < 1 || ny < 1 || nz < 1)
+        return pw_fail(PW_ERR_SHAPE, "bad sizes nx=%d ny=%d nz=%d", nx, ny, nz);
+    if (nz > PW_NOALLOC_MAX_NZ)
+        return pw_fail(PW_ERR_SHAPE, "nz=%d exceeds the no-allocation limit PW_NOALLOC_MAX_NZ=%d", nz,
+                       PW_NOALLOC_MAX_NZ);
+    if (nzp < nz || nzp % 8 != 0)
+        return pw_fail(PW_ERR_SHAPE, "nzp=%d must be >= nz and a multiple of 8", nzp);
+    if ((int64_t)(nx + 4) * (ny + 4) > (int64_t)1 << 31)
+        return pw_fail(PW_ERR_SHAPE, "horizontal size too large");
+    if (dtype != PW_F64 && dtype != PW_F32 && dtype != PW_BF16)
+        return pw_fail(PW_ERR_DTYPE, "unknown dtype %d", (int)dtype);
+    if (!w_uv || !w_w || !out) return pw_fail(PW_ERR_ARG, "w_uv, w_w and out must not be NULL");
+    const void *ps[6] = {u, v, w, su, sv, sw};
+    const char *nm[6] = {"u", "v", "w", "su", "sv", "sw"};
+    for (int q = 0; q < 6; q++) {
+        pw_status s = pw_check_ptr(ps[q], nm[q]);
+        if (s != PW_OK) return s;
+    }
+    double *scratch = nullptr;
+    pw_status s = pw_noalloc_scratch_ptr(&scratch);
+    if (s != PW_OK) return s;
+    double *partials = scratch;                         // every entry rewritten by pass 1
+    double *final_sums = scratch + PW_RED_BLOCKS * 12;  // rewritten by pass 2
+    double *wuv = final_sums + 12, *ww = wuv + PW_NOALLOC_MAX_NZ;
+    cudaStream_t st = (cudaStream_t)stream;
+    PW_CUDA(cudaMemcpyAsync(wuv, w_uv, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, st));
+    PW_CUDA(cudaMemcpyAsync(ww, w_w, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, st));
+    s = pw_launch_residuals_raw(nx, ny, nz, nzp, dtype, wuv, ww, u, v, w, su, sv, sw, partials, final_sums, st);
+    if (s != PW_OK) return s;
+    PW_CUDA(cudaMemcpyAsync(out, final_sums, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PW_CUDA(cudaStreamSynchronize(st));
+    return PW_OK;
+}
