@@ -146,13 +146,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest value over ranks (the slowest rank's time)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(points_per_rank, world, steps, seconds):
+    """Weak scaling: every rank advects its own replica; the job's rate is all
+    ranks' points over the slowest rank's time."""
+    return world * points_per_rank * steps / seconds
 
 
 def time_steps(step, steps, warmup, world, events_for=None):
@@ -221,7 +229,7 @@ def run_gpu(args):
         total, kern_ms = time_steps(make_step(m64, U64, S64), args.steps, args.warmup, world)
     clocks = clk.summary()
     assert m64.device_status() == 0, "device wait timed out"
-    value = world * pts * args.steps / total
+    value = whole_job_rate(pts, world, args.steps, total)
     achieved = BYTES_PER_POINT[hd] * pts / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": recorded_traffic(f"pw_advect_{hd}_{args.algo}"),
@@ -263,6 +271,14 @@ def run_gpu(args):
         re = [float(sums[q, 0] / sums[q, 1]) for q in range(3)]
         rm = [float(sums[q, 2] / sums[q, 3]) for q in range(3)]
         extras["residuals"] = {"ms_per_call": round(dt * 1e3, 3), "R_E": re, "R_M": rm}
+
+    if not args.no_extras and hd == "f64":
+        extras["batched"] = bench_batched(args, world, hbm)
+        torch.cuda.empty_cache()
+        extras["adjoint_loop"] = bench_adjoint_loop(args)
+        torch.cuda.empty_cache()
+        extras["precision"] = bench_precision()
+        torch.cuda.empty_cache()
 
     # ---------------- e2e: pinned host buffers through the public API --------
     host_in = [torch.empty(m64.shape, dtype=m64.in_dtype, pin_memory=True) for _ in range(3)]
@@ -309,6 +325,126 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------
+# extra rows: batched ensemble, adjoint loop, precision study
+# ----------------------------------------------------------------------------
+def bench_batched(args, world, hbm):
+    """64 uneven FP32 subdomains in one persistent launch: autotuned tile shape,
+    halo fill + advect captured in a CUDA graph, replayed K times."""
+    import tempfile as tf
+
+    import torch
+    from paper_2009_12850_b300 import api
+    members = synthetic.ensemble(64)
+    meshes, fields, sources, pts = [], [], [], 0
+    for mb in members:
+        m = api.Mesh(mb.nx, mb.ny, mb.nz, mb.dx, mb.dx, dtype="f32")
+        f = synthetic.wind_fields(mb.nx, mb.ny, mb.nz, mb.seed)
+        meshes.append(m)
+        fields.append([m.from_interior(a) for a in f])
+        sources.append([m.empty_out() for _ in range(3)])
+        pts += mb.nx * mb.ny * mb.nz
+    b = api.Batch(meshes)
+    b.bind(fields, sources)
+    with tf.TemporaryDirectory() as d:
+        tune_ms = b.autotune(os.path.join(d, "tune.txt"))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        b.halo(stream=side)
+        b.advect(stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.halo()
+        b.advect()
+    steps = max(5, args.steps)
+    total, _ = time_steps(lambda rec: graph.replay(), steps, 3, world)
+    assert b.status() == 0
+    # the same work as one launch per member (no batching, no graph)
+    def loop_step(rec):
+        for m, f, s in zip(meshes, fields, sources):
+            m.halo(*f)
+            m.advect(*f, *s)
+    loop_total, _ = time_steps(loop_step, max(3, steps // 2), 2, world)
+    per = total / steps
+    per_loop = loop_total / max(3, steps // 2)
+    return {"workload": "64 members, nx,ny in 32..384 (x8), nz in 64..160, dx in 25..100 m, FP32",
+            "points_per_step": pts, "value": world * pts / per, "unit": UNIT, "ms_per_step": round(per * 1e3, 4),
+            "hbm_frac": round(24 * pts / per / 1e9 / hbm, 4), "autotune_ms": round(tune_ms, 4),
+            "per_member_launch_ms_per_step": round(per_loop * 1e3, 4),
+            "speedup_vs_per_member_launches": round(per_loop / per, 3),
+            "gpu_launches_per_step": 3}
+
+
+def bench_adjoint_loop(args):
+    """Loss = sum of squared sources after 10 Euler steps (dt = 0.5 s) on
+    256 x 256 x 96 FP32 and its gradient by the adjoint kernels with
+    checkpointed recomputation every 2 steps; gradient compared with the same
+    computation in FP64 (native FP64 kernels)."""
+    import torch
+    from paper_2009_12850_b300 import api, autograd
+    wl = synthetic.ADJOINT
+    f = synthetic.wind_fields(wl.nx, wl.ny, wl.nz, wl.seed)
+    dt, steps, every = wl.extra["dt"], wl.extra["steps"], wl.extra["checkpoint_every"]
+    out = {}
+    grads = {}
+    for dtype, algo in (("f32", "auto"), ("f64", "native")):
+        m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype, algo=algo)
+        base = [m.from_interior(a) for a in f]
+
+        def one():
+            U = [t.clone().requires_grad_(True) for t in base]
+            L = autograd.source_energy_loss(m, *U, dt=dt, steps=steps, checkpoint_every=every)
+            L.backward()
+            return L, U
+        L, U = one()
+        torch.cuda.synchronize()
+        reps = 3 if dtype == "f32" else 1
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            L, U = one()
+        e1.record()
+        torch.cuda.synchronize()
+        out[dtype] = {"ms_per_loss_and_grad": round(e0.elapsed_time(e1) / reps, 3), "loss": float(L.item())}
+        grads[dtype] = [m.interior(u.grad).double() for u in U]
+        del m, base, U
+    rel = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(grads["f32"], grads["f64"])]
+    return {"workload": wl.name, "steps": steps, "dt": dt, "checkpoint_every": every,
+            "f32": out["f32"], "f64_native": out["f64"],
+            "grad_rel_err_f32_vs_f64": {"gu": rel[0], "gv": rel[1], "gw": rel[2]}}
+
+
+def bench_precision():
+    """512 x 512 x 160 sheared turbulence: FP32 and BF16 storage against the
+    FP64 split path (itself within 1e-12 of the oracle), max and RMS error per
+    source, and the conservation residuals of each."""
+    import torch
+    from paper_2009_12850_b300 import api
+    wl = synthetic.PRECISION
+    f = synthetic.fields_for(wl)
+    res = {}
+    ref = None
+    for dtype in ("f64", "f32", "bf16"):
+        m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype)
+        U = [m.from_interior(a) for a in f]
+        S = m.advect(*U)
+        sums = m.residual_sums(*U, *S)
+        entry = {"R_E": [float(sums[q, 0] / sums[q, 1]) for q in range(3)],
+                 "R_M": [float(sums[q, 2] / sums[q, 3]) for q in range(3)]}
+        if dtype == "f64":
+            ref = [m.interior(t).clone() for t in S]
+        else:
+            for q, nm in enumerate(("su", "sv", "sw")):
+                d = (m.interior(S[q]).double() - ref[q]).abs()
+                entry[nm] = {"max_abs": float(d.max()), "rms": float(d.pow(2).mean().sqrt()),
+                             "max_rel_to_max": float(d.max() / ref[q].abs().max())}
+        res[dtype] = entry
+        del m, U, S
+    return {"workload": wl.name, "fields": "u = 15 z/z_top + N(0,2), v = N(0,2), w = N(0,0.3) m/s", **res}
 
 
 # ----------------------------------------------------------------------------

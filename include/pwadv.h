@@ -272,6 +272,12 @@ pw_status pw_batch_set_fields(pw_batch *batch, void *const *u, void *const *v, v
  * pull tiles from a device work counter that this call resets on `stream`. */
 pw_status pw_advect_batched(pw_batch *batch, int beta, void *stream);
 
+/* Tile configuration of the batched launch: CTA size (threads, a multiple of 32
+ * in 32..512; each member's tile has threads / (ceil(nz/4)) rows) and columns
+ * marched per tile (tile_i).  Rebuilds the device tables; synchronises
+ * `stream`.  On failure the previous configuration stays in force. */
+pw_status pw_batch_set_tile(pw_batch *batch, int threads, int tile_i, void *stream);
+
 /* Periodic halo fill of the bound u, v, w of every member in one launch. */
 pw_status pw_batch_halo(pw_batch *batch, void *stream);
 

@@ -221,5 +221,8 @@ class Batch:
     def autotune(self, cache_path=None, stream=None):
         return L.pw_batch_autotune(self.handle, cache_path, _stream(stream))
 
+    def set_tile(self, threads, tile_i, stream=None):
+        L.pw_batch_set_tile(self.handle, threads, tile_i, _stream(stream))
+
     def status(self, clear=True, stream=None):
         return L.pw_batch_status(self.handle, clear, _stream(stream))

@@ -151,6 +151,11 @@ static size_t pw_member_smem(const PwGeom &g) {
     return (size_t)g.ns * 3 * g.field_stride * sizeof(float) + (size_t)g.ns * sizeof(uint64_t);
 }
 
+// device array of the 3n bound field pointers used by the batched halo fill
+static void **pw_batch_field_table(pw_batch_impl &b) {
+    return reinterpret_cast<void **>(reinterpret_cast<char *>(b.status) + 64);
+}
+
 // (re)build member descriptors for the current tile configuration and upload
 static pw_status pw_batch_build(pw_batch_impl &b, cudaStream_t st) {
     const int n = b.n;
@@ -203,6 +208,15 @@ static pw_status pw_batch_build(pw_batch_impl &b, cudaStream_t st) {
     if (per_sm < 1) return pw_fail(PW_ERR_SHAPE, "batch kernel cannot be resident with %d threads", b.threads);
     b.grid = std::min(b.total_tiles, per_sm * b.meshes[0]->num_sms);
     PW_CUDA(cudaMemcpyAsync(b.dev, b.host.data(), sizeof(PwBatchMember) * n, cudaMemcpyHostToDevice, st));
+    if (b.bound) {
+        // the halo launch addresses members by slot: its field table must follow
+        // the work order of this build, which changes with the tile shape
+        std::vector<void *> tab(3 * (size_t)n);
+        for (int slot = 0; slot < n; slot++)
+            for (int f = 0; f < 3; f++) tab[3 * slot + f] = b.ptr[f][b.order[slot]];
+        PW_CUDA(cudaMemcpyAsync(pw_batch_field_table(b), tab.data(), sizeof(void *) * 3 * n,
+                                cudaMemcpyHostToDevice, st));
+    }
     PW_CUDA(cudaStreamSynchronize(st));
     return PW_OK;
 }
@@ -251,11 +265,6 @@ extern "C" void pw_batch_destroy(pw_batch *bb) {
     delete bb;
 }
 
-// device array of the 3n bound field pointers used by the batched halo fill
-static void **pw_batch_field_table(pw_batch_impl &b) {
-    return reinterpret_cast<void **>(reinterpret_cast<char *>(b.status) + 64);
-}
-
 extern "C" pw_status pw_batch_set_fields(pw_batch *bb, void *const *u, void *const *v, void *const *w,
                                          void *const *su, void *const *sv, void *const *sw, void *stream) {
     if (!bb) return pw_fail(PW_ERR_ARG, "batch is NULL");
@@ -273,20 +282,26 @@ extern "C" pw_status pw_batch_set_fields(pw_batch *bb, void *const *u, void *con
     }
     for (int f = 0; f < 6; f++) b.ptr[f].assign(lists[f], lists[f] + b.n);
     b.bound = true;
-    cudaStream_t st = (cudaStream_t)stream;
-    // field table for the halo launch, in work order
-    std::vector<void *> tab(3 * b.n);
-    pw_status s = pw_batch_build(b, st);
+    pw_status s = pw_batch_build(b, (cudaStream_t)stream);
+    if (s != PW_OK) b.bound = false;
+    return s;
+}
+
+extern "C" pw_status pw_batch_set_tile(pw_batch *bb, int threads, int tile_i, void *stream) {
+    if (!bb) return pw_fail(PW_ERR_ARG, "batch is NULL");
+    if (threads < 32 || threads > 512 || threads % 32 != 0 || tile_i < 1 || tile_i > 1 << 20)
+        return pw_fail(PW_ERR_ARG, "threads must be a multiple of 32 in 32..512 and tile_i >= 1");
+    pw_batch_impl &b = bb->impl;
+    const int ot = b.threads, oi = b.tile_i;
+    b.threads = threads;
+    b.tile_i = tile_i;
+    pw_status s = pw_batch_build(b, (cudaStream_t)stream);
     if (s != PW_OK) {
-        b.bound = false;
-        return s;
+        b.threads = ot;
+        b.tile_i = oi;
+        pw_batch_build(b, (cudaStream_t)stream);
     }
-    for (int slot = 0; slot < b.n; slot++)
-        for (int f = 0; f < 3; f++) tab[3 * slot + f] = b.ptr[f][b.order[slot]];
-    PW_CUDA(cudaMemcpyAsync(pw_batch_field_table(b), tab.data(), sizeof(void *) * 3 * b.n,
-                            cudaMemcpyHostToDevice, st));
-    PW_CUDA(cudaStreamSynchronize(st));
-    return PW_OK;
+    return s;
 }
 
 static pw_status pw_batch_launch(pw_batch_impl &b, int beta, cudaStream_t st) {

@@ -1,0 +1,56 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks, barrier, the max-over-ranks
+time and the whole-job weak-scaling rate (no GPU)."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.barrier(world)
+    t = bench.max_over_ranks(1.0 + rank, world)
+    rate = bench.whole_job_rate(1000, world, 10, t)
+    out.put((rank, t, rate))
+    dist.destroy_process_group()
+
+
+def test_two_rank_timing_aggregation():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [2.0, 2.0]          # both see the slowest rank
+    assert res[0][2] == pytest.approx(2 * 1000 * 10 / 2.0)
+
+
+def test_reference_arm_rank_gating(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        steps, warmup = 1, 3
+    bench.run_reference(A())     # non-zero ranks exit without work
+    assert capsys.readouterr().out == ""
