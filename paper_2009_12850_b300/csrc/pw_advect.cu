@@ -15,8 +15,9 @@ pw_advect_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
                 int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (pw_status_failed(status)) return;  // sticky failure: do nothing until cleared
-    pw_march_tile<TS, TC, TO, KV>(&mu, &mv, &mw, su, sv, sw, coef, g, beta, status, smem_raw,
-                                  blockIdx.x * g.tj, blockIdx.y * g.ti, blockIdx.z * g.kc);
+    pw_march_tile<TS, TC, TO, KV, PW_MARCH_NS>(&mu, &mv, &mw, su, sv, sw, coef, g, beta, status,
+                                               smem_raw, blockIdx.x * g.tj, blockIdx.y * g.ti,
+                                               blockIdx.z * g.kc);
 }
 
 // --------------------------------------------------------------------------
@@ -93,13 +94,13 @@ pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const
             if (m->algo == PW_ALGO_F64_SPLIT)
                 return pw_launch_advect_split(m, u, v, w, su, sv, sw, beta, st, tile_j, tile_i);
             return pw_launch_march<double, double, double, 2>(m, u, v, w, su, sv, sw, beta, st,
-                                                              tile_j, tile_i, 5);
+                                                              tile_j, tile_i, PW_MARCH_NS);
         case PW_F32:
             return pw_launch_march<float, float, float, 4>(m, u, v, w, su, sv, sw, beta, st, tile_j,
-                                                           tile_i, 5);
+                                                           tile_i, PW_MARCH_NS);
         case PW_BF16:
             return pw_launch_march<__nv_bfloat16, float, float, 4>(m, u, v, w, su, sv, sw, beta, st,
-                                                                   tile_j, tile_i, 5);
+                                                                   tile_j, tile_i, PW_MARCH_NS);
     }
     return pw_fail(PW_ERR_DTYPE, "unknown dtype");
 }

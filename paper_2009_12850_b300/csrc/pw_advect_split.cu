@@ -279,8 +279,8 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
                                  void *su, void *sv, void *sw, int beta, cudaStream_t st,
                                  int tile_j, int tile_i) {
     constexpr int NS = 5;
-    constexpr int TJ = 8;  // the split kernel is compiled for 8 rows of columns per CTA
-    tile_j = TJ;
+    // compiled for 4 or 8 rows of columns per CTA (the nearest of the two is used)
+    tile_j = tile_j <= 5 ? 4 : 8;
     PwSplitGeom g;
     g.nx = m->nx;
     g.ny = m->ny;
@@ -301,6 +301,7 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
     const int threads = (g.kc / 2) * tile_j;
     if (threads > 256)
         return pw_fail(PW_ERR_SHAPE, "split kernel: tile_j=%d needs %d threads (max 256)", tile_j, threads);
+    (void)NS;
     static_assert(NS * sizeof(uint64_t) <= 64, "barrier slot");
     const size_t smem = (size_t)NS * 3 * g.field_stride * 8 + 64 +
                         ((size_t)(g.kc / 2) * 6 + 2) * sizeof(float4);
@@ -311,7 +312,8 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
         pw_status s = pw_make_field_map(&maps[q], f[q], PW_F64, m->nx, m->ny, m->nzp, g.kb, tile_j + 2);
         if (s != PW_OK) return s;
     }
-    auto kern = beta ? pw_advect_split_kernel<NS, TJ, true> : pw_advect_split_kernel<NS, TJ, false>;
+    auto kern = tile_j == 4 ? (beta ? pw_advect_split_kernel<NS, 4, true> : pw_advect_split_kernel<NS, 4, false>)
+                            : (beta ? pw_advect_split_kernel<NS, 8, true> : pw_advect_split_kernel<NS, 8, false>);
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)((m->nz + g.kc - 1) / g.kc));

@@ -50,7 +50,7 @@ struct pw_batch {
     pw_batch_impl impl;
 };
 
-static constexpr int PW_BATCH_NS = 5;
+static constexpr int PW_BATCH_NS = PW_MARCH_NS;
 
 __global__ void __launch_bounds__(512)
 pw_batch_kernel(const PwBatchMember *__restrict__ members, int n, int total_tiles,
@@ -75,7 +75,7 @@ pw_batch_kernel(const PwBatchMember *__restrict__ members, int n, int total_tile
         const int tjx = local % M.tiles_j;
         local /= M.tiles_j;
         const int tix = local % M.tiles_i, tkx = local / M.tiles_i;
-        if (!pw_march_tile<float, float, float, 4>(&M.maps[0], &M.maps[1], &M.maps[2], M.su, M.sv,
+        if (!pw_march_tile<float, float, float, 4, PW_MARCH_NS>(&M.maps[0], &M.maps[1], &M.maps[2], M.su, M.sv,
                                                    M.sw, M.coef, g, beta, status, smem_raw,
                                                    tjx * g.tj, tix * g.ti, tkx * g.kc))
             return;
@@ -422,10 +422,10 @@ extern "C" pw_status pw_autotune(pw_mesh *m, const void *u, const void *v, const
         if (best_ms) *best_ms = -1.0f;
         return s;
     }
-    std::vector<int> cj, ci = {8, 16, 32, 64, 128};
-    if (m->dtype == PW_F64 && m->algo == PW_ALGO_F64_SPLIT) cj = {8};
+    std::vector<int> cj, ci = {16, 32, 64, 128, 256};
+    if (m->dtype == PW_F64 && m->algo == PW_ALGO_F64_SPLIT) cj = {4, 8};
     else if (m->dtype == PW_F64) cj = {2, 4, 8};
-    else cj = {4, 8, 16};
+    else cj = {2, 4, 8};
     float best = 1e30f;
     int bj = m->tile_j, bi = m->tile_i;
     for (int a : cj)
@@ -468,8 +468,8 @@ extern "C" pw_status pw_batch_autotune(pw_batch *bb, const char *cache_path, voi
     }
     float best = 1e30f;
     int bt = b.threads, bi = b.tile_i;
-    for (int t : {128, 256, 384, 512})
-        for (int c : {8, 16, 32, 64}) {
+    for (int t : {64, 128, 256, 384})
+        for (int c : {16, 32, 64, 128}) {
             b.threads = t;
             b.tile_i = c;
             pw_status s = pw_batch_build(b, st);

@@ -18,6 +18,9 @@
 
 #include "pw_internal.h"
 
+// planes in the shared-memory ring of the x-march (NS - 3 planes of prefetch)
+#define PW_MARCH_NS 5
+
 struct PwGeom {
     int nx, ny, nz, nzp;
     int kc;            // k chunk per CTA (multiple of KV and of the k halo)
@@ -112,12 +115,57 @@ __device__ __forceinline__ void pw_store(TO *p, const TO (&r)[KV], int nvalid, i
 }
 
 // --------------------------------------------------------------------------
+// k edges of a thread's slab: the value below comes from the thread holding the
+// previous slab of the same column (one lane down), the value above from the
+// next slab's thread (one lane up), by warp shuffles; threads at the ends of a
+// column (or of a warp) read those values from shared memory instead.
+// --------------------------------------------------------------------------
+template <typename TS, typename TC, int KV>
+__device__ __forceinline__ void pw_col_edges(const TS *row, int kk, TC (&x)[KV + 2], unsigned mask,
+                                             bool lo_shfl, bool hi_shfl, bool want_lo, bool want_hi) {
+    SlabLoad<TS, TC, KV>::run(row + kk, x + 1);
+    if (want_lo) {
+        const TC up = __shfl_up_sync(mask, x[KV], 1);
+        if (lo_shfl) x[0] = up;
+        else x[0] = pw_to<TC>(row[kk - 1]);
+    } else {
+        x[0] = TC(0);
+    }
+    if (want_hi) {
+        const TC dn = __shfl_down_sync(mask, x[1], 1);
+        if (hi_shfl) x[KV + 1] = dn;
+        else x[KV + 1] = pw_to<TC>(row[kk + KV]);
+    } else {
+        x[KV + 1] = TC(0);
+    }
+}
+
+// levels at or above kz read 0 (padding k >= nz; for w also the lid nz-1)
+template <typename TC, int KV>
+__device__ __forceinline__ void pw_zero_from(TC (&x)[KV + 2], int kbase, int kz) {
+#pragma unroll
+    for (int m = 0; m < KV + 2; m++)
+        if (kbase - 1 + m >= kz) x[m] = TC(0);
+}
+
+template <typename TC, int KV>
+__device__ __forceinline__ void pw_copy(TC (&d)[KV + 2], const TC (&s)[KV + 2]) {
+#pragma unroll
+    for (int m = 0; m < KV + 2; m++) d[m] = s[m];
+}
+
+// --------------------------------------------------------------------------
 // one tile of the x-march: tile_j rows from j0, columns i0 .. i0+tile_i-1, the
-// k chunk starting at k0.  Shared memory: ns plane slots then ns mbarriers
+// k chunk starting at k0.  Shared memory: NS plane slots then NS mbarriers
 // (initialised here, invalidated before returning so the caller may run the
 // next tile).  Returns false if a TMA wait timed out (status recorded).
+//
+// Register window along x: the centre-row columns of planes i-1 and i and the
+// side rows' values that the next step needs are carried in registers, so a
+// step loads only column i+1 of the centre row and the rows j-1, j+1 it still
+// lacks (9 slabs and 8 edge values instead of 17 slabs and 9 edges).
 // --------------------------------------------------------------------------
-template <typename TS, typename TC, typename TO, int KV>
+template <typename TS, typename TC, typename TO, int KV, int NS>
 __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUtensorMap *mv_,
                                               const CUtensorMap *mw_, TO *__restrict__ su,
                                               TO *__restrict__ sv, TO *__restrict__ sw,
@@ -126,157 +174,189 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
                                               int j0, int i0, int k0) {
     const CUtensorMap &mu = *mu_, &mv = *mv_, &mw = *mw_;
     TS *planes = reinterpret_cast<TS *>(smem_raw);
-    uint64_t *bars =
-        reinterpret_cast<uint64_t *>(smem_raw + (size_t)g.ns * 3 * g.field_stride * sizeof(TS));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * 3 * g.field_stride * sizeof(TS));
+    const int fs = g.field_stride;
 
     const int nkt = g.kc / KV;
-    const int tk = threadIdx.x % nkt, tj = threadIdx.x / nkt;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tk = tid % nkt, tj = tid / nkt;
     const int i_end = min(i0 + g.ti, g.nx);
     const int nplanes = i_end - i0 + 2;  // planes i0-1 .. i_end
     const uint32_t plane_bytes = 3u * (uint32_t)g.plane_elems * (uint32_t)sizeof(TS);
     const int kbase = k0 + tk * KV;      // first level of this thread
     const int kk = g.h + tk * KV;        // its position inside a plane row
     const int j = j0 + tj;
+    const bool in_tile = tj < g.tj;
+    const int tjc = in_tile ? tj : g.tj - 1;  // rows read by threads outside the tile stay in the plane
+    const bool active = in_tile && (j < g.ny) && (kbase < g.nz);
+    const bool top = kbase + KV >= g.nz - 1;  // slab touches the lid or the padding
+    const int nvalid = g.nz - kbase;
+    // shuffle partners: same column, same warp; lanes of a partial last warp
+    const int wbase = tid & ~31;
+    const unsigned mask = (int)blockDim.x - wbase >= 32 ? 0xffffffffu
+                                                         : ((1u << ((int)blockDim.x - wbase)) - 1u);
+    const bool lo_shfl = tk > 0 && lane > 0;
+    const bool hi_shfl = tk < nkt - 1 && lane < 31 && tid + 1 < (int)blockDim.x;
 
     if (threadIdx.x == 0) {
         pw_prefetch_map(&mu);
         pw_prefetch_map(&mv);
         pw_prefetch_map(&mw);
-        for (int s = 0; s < g.ns; s++) pw_mbar_init(&bars[s], 1);
+        for (int s = 0; s < NS; s++) pw_mbar_init(&bars[s], 1);
         pw_fence_barrier_init();
     }
     __syncthreads();
 
     auto issue = [&](int p) {
-        int s = p % g.ns;
-        TS *dst = planes + (size_t)s * 3 * g.field_stride;
+        const int s = p % NS;
+        TS *dst = planes + (size_t)s * 3 * fs;
         pw_mbar_expect_tx(&bars[s], plane_bytes);
-        int c0 = k0 - g.h, c1 = j0 + 1, c2 = i0 + 1 + p;  // (k, j-1, i-1+p) + halo offset
+        const int c0 = k0 - g.h, c1 = j0 + 1, c2 = i0 + 1 + p;  // (k, j-1, i-1+p) + halo offset
         pw_tma_load_3d(dst, &mu, c0, c1, c2, &bars[s]);
-        pw_tma_load_3d(dst + g.field_stride, &mv, c0, c1, c2, &bars[s]);
-        pw_tma_load_3d(dst + 2 * g.field_stride, &mw, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + fs, &mv, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + 2 * fs, &mw, c0, c1, c2, &bars[s]);
     };
     int issued = 0;  // planes handed to TMA (thread 0's count)
     if (threadIdx.x == 0) {
-        for (int p = 0; p < min(g.ns, nplanes); p++) issue(p);
-        issued = min(g.ns, nplanes);
+        for (int p = 0; p < min(NS, nplanes); p++) issue(p);
+        issued = min(NS, nplanes);
     }
+    auto slot = [&](int p) { return planes + (size_t)(p % NS) * 3 * fs; };
+    auto give_up = [&](int waited) {
+        if (threadIdx.x == 0) {
+            for (int p = waited; p < issued; p++)
+                if (!pw_mbar_wait_bounded(&bars[p % NS], (uint32_t)((p / NS) & 1), PW_DRAIN_CYCLES)) break;
+            atomicExch(status, (int)PW_ERR_TIMEOUT);
+        }
+    };
 
     // vertical coefficients of this thread's levels (0 beyond nz)
     TC c1[KV], c2[KV], d1[KV], d2[KV];
 #pragma unroll
     for (int m = 0; m < KV; m++) {
-        int k = kbase + m;
-        bool in = k < g.nz;
+        const int k = kbase + m;
+        const bool in = k < g.nz;
         c1[m] = in ? coef[k] : TC(0);
         c2[m] = in ? coef[g.nz + k] : TC(0);
         d1[m] = in ? coef[2 * g.nz + k] : TC(0);
         d2[m] = in ? coef[3 * g.nz + k] : TC(0);
     }
     const TC tcx = (TC)g.tcx, tcy = (TC)g.tcy;
-    const bool active = (tj < g.tj) && (j < g.ny) && (kbase < g.nz);
-    const bool top = kbase + KV >= g.nz - 1;  // slab touches the lid or the padding
-    const int nvalid = g.nz - kbase;
-    const int row_len = g.kb;
+    const int L = g.kb;
+    const int rS = tjc * L, rC = (tjc + 1) * L, rN = (tjc + 2) * L;
+    const int zu = g.nz, zw = g.nz - 1;
 
-    int waited = 0;
+    // the window: planes 0 (column i0-1) and 1 (column i0)
+    TC uM[KV + 2], uC[KV + 2], vM[KV + 2], vC[KV + 2], wM[KV + 2], wC[KV + 2], vS[KV + 2], uNM[KV + 2];
+    {
+        const bool ok = pw_mbar_wait_bounded(&bars[0], 0) && pw_mbar_wait_bounded(&bars[1], 0);
+        if (!__syncthreads_and(ok)) {
+            give_up(0);
+            return false;
+        }
+        const TS *P0 = slot(0), *P1 = slot(1);
+        pw_col_edges<TS, TC, KV>(P0 + rC, kk, uM, mask, lo_shfl, hi_shfl, false, true);
+        pw_col_edges<TS, TC, KV>(P1 + rC, kk, uC, mask, lo_shfl, hi_shfl, true, true);
+        pw_col_edges<TS, TC, KV>(P0 + fs + rC, kk, vM, mask, lo_shfl, hi_shfl, false, false);
+        pw_col_edges<TS, TC, KV>(P1 + fs + rC, kk, vC, mask, lo_shfl, hi_shfl, true, true);
+        pw_col_edges<TS, TC, KV>(P0 + 2 * fs + rC, kk, wM, mask, lo_shfl, hi_shfl, false, false);
+        pw_col_edges<TS, TC, KV>(P1 + 2 * fs + rC, kk, wC, mask, lo_shfl, hi_shfl, true, true);
+        pw_col_edges<TS, TC, KV>(P1 + fs + rS, kk, vS, mask, lo_shfl, hi_shfl, false, true);
+        pw_col_edges<TS, TC, KV>(P0 + rN, kk, uNM, mask, lo_shfl, hi_shfl, false, false);
+        if (top) {
+            pw_zero_from<TC, KV>(uM, kbase, zu);
+            pw_zero_from<TC, KV>(uC, kbase, zu);
+            pw_zero_from<TC, KV>(vM, kbase, zu);
+            pw_zero_from<TC, KV>(vC, kbase, zu);
+            pw_zero_from<TC, KV>(wM, kbase, zw);
+            pw_zero_from<TC, KV>(wC, kbase, zw);
+            pw_zero_from<TC, KV>(vS, kbase, zu);
+            pw_zero_from<TC, KV>(uNM, kbase, zu);
+        }
+    }
+
+    int waited = 2;
     for (int i = i0; i < i_end; i++) {
         const int q = i - i0 + 1;  // plane index of column i
         bool ok = true;
-        while (waited <= q + 1 && ok) {
-            ok = pw_mbar_wait_bounded(&bars[waited % g.ns], (uint32_t)((waited / g.ns) & 1));
-            if (ok) waited++;
+        if (waited <= q + 1) {
+            ok = pw_mbar_wait_bounded(&bars[(q + 1) % NS], (uint32_t)(((q + 1) / NS) & 1));
+            if (ok) waited = q + 2;
         }
         if (!__syncthreads_and(ok)) {
-            // give up: wait (bounded) for copies still in flight, record, leave
-            if (threadIdx.x == 0) {
-                for (int p = waited; p < issued; p++)
-                    if (!pw_mbar_wait_bounded(&bars[p % g.ns], (uint32_t)((p / g.ns) & 1),
-                                              PW_DRAIN_CYCLES))
-                        break;
-                atomicExch(status, (int)PW_ERR_TIMEOUT);
-            }
+            give_up(waited);
             return false;
         }
         // everyone is past step i-1: the slot of plane q-2 is free
-        if (threadIdx.x == 0 && q >= 2 && q - 2 + g.ns < nplanes) {
-            issue(q - 2 + g.ns);
-            issued = q - 1 + g.ns;
+        if (threadIdx.x == 0 && q >= 2 && q - 2 + NS < nplanes) {
+            issue(q - 2 + NS);
+            issued = q - 1 + NS;
         }
-        if (!active) continue;
+        const TS *Pc = slot(q), *Pp = slot(q + 1);
 
-        const TS *Pm = planes + (size_t)((q - 1) % g.ns) * 3 * g.field_stride;
-        const TS *Pc = planes + (size_t)(q % g.ns) * 3 * g.field_stride;
-        const TS *Pp = planes + (size_t)((q + 1) % g.ns) * 3 * g.field_stride;
-        const int fs = g.field_stride;
-        const int rS = tj * row_len, rC = (tj + 1) * row_len, rN = (tj + 2) * row_len;
-
-        TC uC[KV + 2], uM[KV + 2], uP[KV + 2], vC[KV + 2], vM[KV + 2], vP[KV + 2];
-        TC wC[KV + 2], wM[KV + 2], wP[KV + 2];
-        TC uS[KV + 2], vS[KV + 2], vSP[KV + 2], wS[KV + 2];
-        TC uN[KV + 2], uNM[KV + 2], vN[KV + 2], wN[KV + 2];
-        pw_col<TS, TC, KV, true, true>(Pc + rC, kk, uC);
-        pw_col<TS, TC, KV, false, true>(Pm + rC, kk, uM);
-        pw_col<TS, TC, KV, false, false>(Pp + rC, kk, uP);
-        pw_col<TS, TC, KV, true, true>(Pc + fs + rC, kk, vC);
-        pw_col<TS, TC, KV, false, false>(Pm + fs + rC, kk, vM);
-        pw_col<TS, TC, KV, false, false>(Pp + fs + rC, kk, vP);
-        pw_col<TS, TC, KV, true, true>(Pc + 2 * fs + rC, kk, wC);
-        pw_col<TS, TC, KV, false, false>(Pm + 2 * fs + rC, kk, wM);
-        pw_col<TS, TC, KV, true, false>(Pp + 2 * fs + rC, kk, wP);
-        pw_col<TS, TC, KV, false, false>(Pc + rS, kk, uS);
-        pw_col<TS, TC, KV, false, true>(Pc + fs + rS, kk, vS);
-        pw_col<TS, TC, KV, false, false>(Pp + fs + rS, kk, vSP);
-        pw_col<TS, TC, KV, false, false>(Pc + 2 * fs + rS, kk, wS);
-        pw_col<TS, TC, KV, false, false>(Pc + rN, kk, uN);
-        pw_col<TS, TC, KV, false, false>(Pm + rN, kk, uNM);
-        pw_col<TS, TC, KV, false, false>(Pc + fs + rN, kk, vN);
-        pw_col<TS, TC, KV, true, false>(Pc + 2 * fs + rN, kk, wN);
-
+        TC uP[KV + 2], vP[KV + 2], wP[KV + 2], uS[KV + 2], wS[KV + 2], vSP[KV + 2];
+        TC uN[KV + 2], vN[KV + 2], wN[KV + 2];
+        pw_col_edges<TS, TC, KV>(Pp + rC, kk, uP, mask, lo_shfl, hi_shfl, true, true);
+        pw_col_edges<TS, TC, KV>(Pp + fs + rC, kk, vP, mask, lo_shfl, hi_shfl, true, true);
+        pw_col_edges<TS, TC, KV>(Pp + 2 * fs + rC, kk, wP, mask, lo_shfl, hi_shfl, true, true);
+        pw_col_edges<TS, TC, KV>(Pc + rS, kk, uS, mask, lo_shfl, hi_shfl, false, false);
+        pw_col_edges<TS, TC, KV>(Pc + 2 * fs + rS, kk, wS, mask, lo_shfl, hi_shfl, false, false);
+        pw_col_edges<TS, TC, KV>(Pp + fs + rS, kk, vSP, mask, lo_shfl, hi_shfl, false, true);
+        pw_col_edges<TS, TC, KV>(Pc + rN, kk, uN, mask, lo_shfl, hi_shfl, false, false);
+        pw_col_edges<TS, TC, KV>(Pc + fs + rN, kk, vN, mask, lo_shfl, hi_shfl, false, false);
+        pw_col_edges<TS, TC, KV>(Pc + 2 * fs + rN, kk, wN, mask, lo_shfl, hi_shfl, true, false);
         if (top) {
-            // levels >= nz are padding (0); w on the lid face nz-1 is 0 by definition
-#pragma unroll
-            for (int m = 0; m < KV + 2; m++) {
-                int k = kbase - 1 + m;
-                if (k >= g.nz) {
-                    uC[m] = 0; uM[m] = 0; uP[m] = 0; vC[m] = 0; vM[m] = 0; vP[m] = 0;
-                    uS[m] = 0; vS[m] = 0; vSP[m] = 0; uN[m] = 0; uNM[m] = 0; vN[m] = 0;
-                }
-                if (k >= g.nz - 1) {
-                    wC[m] = 0; wM[m] = 0; wP[m] = 0; wS[m] = 0; wN[m] = 0;
-                }
-            }
+            pw_zero_from<TC, KV>(uP, kbase, zu);
+            pw_zero_from<TC, KV>(vP, kbase, zu);
+            pw_zero_from<TC, KV>(wP, kbase, zw);
+            pw_zero_from<TC, KV>(uS, kbase, zu);
+            pw_zero_from<TC, KV>(wS, kbase, zw);
+            pw_zero_from<TC, KV>(vSP, kbase, zu);
+            pw_zero_from<TC, KV>(uN, kbase, zu);
+            pw_zero_from<TC, KV>(vN, kbase, zu);
+            pw_zero_from<TC, KV>(wN, kbase, zw);
         }
 
-        TO ru[KV], rv[KV], rw[KV];
+        if (active) {
+            TO ru[KV], rv[KV], rw[KV];
 #pragma unroll
-        for (int m = 0; m < KV; m++) {
-            const int a = m + 1;  // index of level kbase+m in the slab arrays
-            TC s;
-            s = tcx * (uM[a] * (uM[a] + uC[a]) - uP[a] * (uC[a] + uP[a]));
-            s = s + tcy * (uS[a] * (vS[a] + vSP[a]) - uN[a] * (vC[a] + vP[a]));
-            s = s + c1[m] * uC[a - 1] * (wC[a - 1] + wP[a - 1]);
-            s = s - c2[m] * uC[a + 1] * (wC[a] + wP[a]);
-            ru[m] = (TO)s;
-            s = tcx * (vM[a] * (uM[a] + uNM[a]) - vP[a] * (uC[a] + uN[a]));
-            s = s + tcy * (vS[a] * (vS[a] + vC[a]) - vN[a] * (vC[a] + vN[a]));
-            s = s + c1[m] * vC[a - 1] * (wC[a - 1] + wN[a - 1]);
-            s = s - c2[m] * vC[a + 1] * (wC[a] + wN[a]);
-            rv[m] = (TO)s;
-            s = tcx * (wM[a] * (uM[a] + uM[a + 1]) - wP[a] * (uC[a] + uC[a + 1]));
-            s = s + tcy * (wS[a] * (vS[a] + vS[a + 1]) - wN[a] * (vC[a] + vC[a + 1]));
-            s = s + d1[m] * wC[a - 1] * (wC[a - 1] + wC[a]);
-            s = s - d2[m] * wC[a + 1] * (wC[a] + wC[a + 1]);
-            rw[m] = (kbase + m < g.nz - 1) ? (TO)s : TO(0);
+            for (int m = 0; m < KV; m++) {
+                const int a = m + 1;  // index of level kbase+m in the slab arrays
+                TC s;
+                s = tcx * (uM[a] * (uM[a] + uC[a]) - uP[a] * (uC[a] + uP[a]));
+                s = s + tcy * (uS[a] * (vS[a] + vSP[a]) - uN[a] * (vC[a] + vP[a]));
+                s = s + c1[m] * uC[a - 1] * (wC[a - 1] + wP[a - 1]);
+                s = s - c2[m] * uC[a + 1] * (wC[a] + wP[a]);
+                ru[m] = (TO)s;
+                s = tcx * (vM[a] * (uM[a] + uNM[a]) - vP[a] * (uC[a] + uN[a]));
+                s = s + tcy * (vS[a] * (vS[a] + vC[a]) - vN[a] * (vC[a] + vN[a]));
+                s = s + c1[m] * vC[a - 1] * (wC[a - 1] + wN[a - 1]);
+                s = s - c2[m] * vC[a + 1] * (wC[a] + wN[a]);
+                rv[m] = (TO)s;
+                s = tcx * (wM[a] * (uM[a] + uM[a + 1]) - wP[a] * (uC[a] + uC[a + 1]));
+                s = s + tcy * (wS[a] * (vS[a] + vS[a + 1]) - wN[a] * (vC[a] + vC[a + 1]));
+                s = s + d1[m] * wC[a - 1] * (wC[a - 1] + wC[a]);
+                s = s - d2[m] * wC[a + 1] * (wC[a] + wC[a + 1]);
+                rw[m] = (kbase + m < g.nz - 1) ? (TO)s : TO(0);
+            }
+            const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
+            pw_store<TO, KV>(su + off, ru, nvalid, beta);
+            pw_store<TO, KV>(sv + off, rv, nvalid, beta);
+            pw_store<TO, KV>(sw + off, rw, nvalid, beta);
         }
-        const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
-        pw_store<TO, KV>(su + off, ru, nvalid, beta);
-        pw_store<TO, KV>(sv + off, rv, nvalid, beta);
-        pw_store<TO, KV>(sw + off, rw, nvalid, beta);
+        // slide the window one column along x
+        pw_copy<TC, KV>(uM, uC);
+        pw_copy<TC, KV>(uC, uP);
+        pw_copy<TC, KV>(vM, vC);
+        pw_copy<TC, KV>(vC, vP);
+        pw_copy<TC, KV>(wM, wC);
+        pw_copy<TC, KV>(wC, wP);
+        pw_copy<TC, KV>(vS, vSP);
+        pw_copy<TC, KV>(uNM, uN);
     }
     __syncthreads();  // every thread is past its last wait: barriers can be reused
     if (threadIdx.x == 0)
-        for (int s = 0; s < g.ns; s++) pw_mbar_inval(&bars[s]);
+        for (int s = 0; s < NS; s++) pw_mbar_inval(&bars[s]);
     __syncthreads();
     return true;
 }
