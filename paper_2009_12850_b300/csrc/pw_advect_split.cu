@@ -134,6 +134,7 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
             if (R < ROWS) conv_chunk(base, R, tk + 1);
         }
         for (int e = tid; e < 2 * ROWS; e += nt) conv_chunk(base, e >> 1, (e & 1) ? nkt + 1 : 0);
+        pw_fence_proxy_async();  // the slot is refilled by TMA later
     };
 
     // coefficients of each level pair of the chunk, prepared once per CTA in

@@ -88,6 +88,12 @@ __device__ __forceinline__ void pw_mbar_inval(uint64_t *bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(pw_smem_u32(bar)) : "memory");
 }
 
+// order this thread's generic-proxy writes to shared memory before later
+// asynchronous-proxy (TMA) writes to the same bytes
+__device__ __forceinline__ void pw_fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void pw_fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
