@@ -122,10 +122,19 @@ pw_status pw_mesh_coefficients(const pw_mesh *mesh, double *out, double *out_h);
 
 /* Read (and with clear != 0 reset) the mesh's device status word: 0, or
  * PW_ERR_TIMEOUT when a kernel gave up waiting on an asynchronous copy since the
- * last clear.  Synchronises `stream`. */
+ * last clear.  The word is sticky: once set, stencil kernels on this mesh
+ * return without work until it is cleared.  Synchronises `stream`. */
 pw_status pw_mesh_device_status(const pw_mesh *mesh, int clear, void *stream, int *status);
 
-/* Tile configuration used by the stencil launches of this mesh: rows of columns
+/* Failure-path self-test: launches a kernel that waits, with the library's
+ * bounded mbarrier wait, for at most `cycles` clock cycles (1 .. 2e9) on a
+ * barrier that nothing completes, and then records PW_ERR_TIMEOUT in the mesh
+ * status word exactly as a stencil kernel that gave up on a copy would.  While
+ * the word is set, stencil launches on the mesh return at once without work;
+ * pw_mesh_device_status(clear = 1) resets it.  Faults nothing; for tests. */
+pw_status pw_selftest_timeout(const pw_mesh *mesh, long long cycles, void *stream);
+
+/* Tile configuration used by the stencil launches of this mesh/* Tile configuration used by the stencil launches of this mesh: rows of columns
  * per CTA (tile_j, 1..32), columns marched per CTA along x (tile_i, >= 1).
  * Set by pw_autotune or by hand; not safe while launches are being enqueued
  * from another thread. */

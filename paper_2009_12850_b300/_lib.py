@@ -53,6 +53,7 @@ _SIGS = {
     "pw_mesh_coefficients": ([_vp, _dp, _dp], _i),
     "pw_mesh_device_status": ([_vp, _i, _vp, _ip], _i),
     "pw_mesh_set_tile": ([_vp, _i, _i], _i),
+    "pw_selftest_timeout": ([_vp, ctypes.c_longlong, _vp], _i),
     "pw_mesh_get_tile": ([_vp, _ip, _ip], _i),
     "pw_halo_periodic": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_halo_fold": ([_vp, _vp, _vp, _vp, _vp], _i),
@@ -133,6 +134,10 @@ def pw_mesh_device_status(mesh, clear, stream):
     st = ctypes.c_int()
     check(_c.pw_mesh_device_status(mesh, int(clear), stream, ctypes.byref(st)), "pw_mesh_device_status")
     return st.value
+
+
+def pw_selftest_timeout(mesh, cycles, stream):
+    check(_c.pw_selftest_timeout(mesh, int(cycles), stream), "pw_selftest_timeout")
 
 
 def pw_mesh_set_tile(mesh, tile_j, tile_i):

@@ -174,6 +174,9 @@ class Mesh:
     def set_tile(self, tile_j, tile_i):
         L.pw_mesh_set_tile(self.handle, tile_j, tile_i)
 
+    def selftest_timeout(self, cycles=20_000_000, stream=None):
+        L.pw_selftest_timeout(self.handle, cycles, _stream(stream))
+
     def get_tile(self):
         return L.pw_mesh_get_tile(self.handle)
 

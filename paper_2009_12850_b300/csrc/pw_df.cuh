@@ -123,5 +123,18 @@ __device__ __forceinline__ double widen(float f) {
     return __hiloint2double((int)h, (int)l);
 }
 
-// hi + lo rounded to double (one FP64 add)
-__device__ __forceinline__ double join(float hi, float lo) { return widen(hi) + widen(lo); }
+// Float -> double by integer widening for normal floats only (no zero or
+// subnormal handling; those come out as a number of magnitude ~2^-127).
+__device__ __forceinline__ double widen_normal(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t h = (((b & 0x7fffffffu) >> 3) + 0x38000000u) | (b & 0x80000000u);
+    return __hiloint2double((int)h, (int)(b << 29));
+}
+
+// hi + lo rounded to double with one FP64 add.  Only the exact-zero case needs
+// care: when hi != 0 a zero or subnormal lo is below half an ulp of any result
+// in range, and when hi == 0 a normal lo is widened exactly.
+__device__ __forceinline__ double join(float hi, float lo) {
+    const double d = widen_normal(hi) + widen_normal(lo);
+    return (hi == 0.0f && lo == 0.0f) ? 0.0 : d;
+}

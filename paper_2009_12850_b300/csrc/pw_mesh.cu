@@ -668,6 +668,29 @@ extern "C" pw_status pw_residuals(const pw_mesh *m, const void *u, const void *v
 }
 
 // ---------------------------------------------------------------------------
+// failure-path self-test: a bounded wait on an mbarrier that nothing completes
+// ---------------------------------------------------------------------------
+__global__ void pw_selftest_timeout_kernel(int *status, long long cycles) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        pw_mbar_init(&bar, 1);
+        pw_fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !pw_mbar_wait_bounded(&bar, 0, cycles)) atomicExch(status, (int)PW_ERR_TIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) pw_mbar_inval(&bar);
+}
+
+extern "C" pw_status pw_selftest_timeout(const pw_mesh *m, long long cycles, void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    if (cycles < 1 || cycles > PW_WAIT_CYCLES) return pw_fail(PW_ERR_ARG, "cycles must be in 1..%lld", PW_WAIT_CYCLES);
+    pw_selftest_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(m->status, cycles);
+    PW_CUDA(cudaGetLastError());
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
 // lid check
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -273,3 +273,32 @@ def test_split_tiles(pw, tile):
     got, _, _ = run_forward(pw, m, f)
     for q in range(3):
         compare("split tile", got[q], ref[q], cond[q], TOL_F64, TOL_F64)
+
+
+@pytest.mark.parametrize("dtype,algo", [("f32", "auto"), ("f64", "split"), ("f64", "native")])
+def test_timeout_status_is_reported_and_sticky(pw, dtype, algo):
+    """A bounded wait that runs out (a barrier nothing completes, ~10 ms) sets
+    PW_ERR_TIMEOUT; while it is set the stencil does nothing; clearing it
+    restores normal operation.  No fault, no hang."""
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz = 20, 16, 12
+    m, f = make(pw, nx, ny, nz, dtype=dtype, algo=algo)
+    U = [m.from_interior(a) for a in f]
+    S = [m.empty_out().fill_(3.0) for _ in range(3)]
+    m.selftest_timeout(20_000_000)
+    torch.cuda.synchronize()
+    assert m.device_status(clear=False) == L.PW_ERR_TIMEOUT
+    m.advect(*U, *S)
+    torch.cuda.synchronize()
+    for s in S:
+        assert torch.all(m.interior(s) == 3.0)       # skipped while the status is set
+    assert m.device_status(clear=True) == L.PW_ERR_TIMEOUT
+    assert m.device_status() == 0
+    m.advect(*U, *S)
+    torch.cuda.synchronize()
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    fr = rounded(f, dtype)
+    ref, cond = oracle.advect(c, *fr, want_cond=True)
+    tol = (TOL_F64, TOL_F64) if dtype == "f64" else (1e-5, TOL_F32_COND)
+    for q in range(3):
+        compare("after clear", m.interior(S[q]).double().cpu().numpy(), ref[q], cond[q], *tol)
