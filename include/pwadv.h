@@ -10,7 +10,9 @@
  *   u(i,j,k) at (x_{i+1/2}, y_j, zn_k), v(i,j,k) at (x_i, y_{j+1/2}, zn_k),
  *   w(i,j,k) at (x_i, y_j, zf_k), zf_k the top face of cell k.
  * w at the ground face (below k = 0) is 0, and the lid face w(.,.,nz-1) is 0 by
- * definition: the value stored there is never read and sw(.,.,nz-1) = 0.
+ * definition: the value stored there is never read and sw(.,.,nz-1) = 0 (for
+ * nz = 1, where w is all lid, its values must be finite: they meet only zero
+ * factors).
  *
  * Field layout.  Every field and source buffer holds (nx+4) * (ny+4) * nzp
  * elements: index ((i+2) * (ny+4) + (j+2)) * nzp + k for i in [-2, nx+2),
@@ -185,8 +187,9 @@ pw_status pw_advect(const pw_mesh *mesh, const void *u, const void *v, const voi
  * Halos of u, v, w must be filled; the interior of gsu, gsv, gsw is read and
  * THEIR HALO COLUMNS ARE OVERWRITTEN with periodic copies.  gw(.,.,nz-1) = 0
  * (the lid is not a degree of freedom).  Only interior points k < nz of
- * gu, gv, gw are written.  FP32 and FP64 meshes (FP64 in native FP64
- * arithmetic); PW_ERR_DTYPE for BF16.  No argument may alias an output. */
+ * gu, gv, gw are written.  For nz = 1 (sw identically 0) gsw is ignored and
+ * overwritten with 0.  FP32 and FP64 meshes (FP64 in native FP64 arithmetic);
+ * PW_ERR_DTYPE for BF16.  No argument may alias an output. */
 pw_status pw_advect_adjoint(const pw_mesh *mesh, const void *u, const void *v, const void *w,
                             void *gsu, void *gsv, void *gsw,
                             void *gu, void *gv, void *gw, double alpha, int beta, void *stream);

@@ -8,8 +8,9 @@
 // n - Q1, n - Q2.  The incoming gradients y = (gsu, gsv, gsw) are read through
 // their periodic halos, so what the forward read through a halo copy lands on
 // the interior point it copies (the adjoint of the halo fill).  Ground and lid
-// rules are enforced by zeroing: values at k < 0 or k >= nz, and w, gsw on the
-// lid face, read as 0, which removes exactly the terms the forward drops.
+// rules come from zeros: values at k < 0 or k >= nz, and w, gsw on the lid
+// face, arrive from TMA as 0 (the tensor maps carry the logical k extent),
+// which removes exactly the terms the forward drops.
 //
 // Same x-march as the forward kernel, with six fields (u, v, w, gsu, gsv, gsw)
 // per shared-memory plane.
@@ -26,15 +27,11 @@ struct PwAdjGeom {
 };
 
 template <typename TS, typename TC, int KV>
-__device__ __forceinline__ void pw_adj_col(const TS *row, int kk, int kbase, int kzero,
-                                           TC (&x)[KV + 2]) {
-    // x[0] = level kbase-1 ... x[KV+1] = level kbase+KV; levels >= kzero read 0
+__device__ __forceinline__ void pw_adj_col(const TS *row, int kk, TC (&x)[KV + 2]) {
+    // x[0] = level kbase-1 ... x[KV+1] = level kbase+KV (levels past the
+    // logical extent arrived from TMA as 0)
 #pragma unroll
-    for (int m = 0; m < KV + 2; m++) {
-        int k = kbase - 1 + m;
-        TC val = pw_to<TC>(row[kk - 1 + m]);
-        x[m] = (k >= kzero) ? TC(0) : val;
-    }
+    for (int m = 0; m < KV + 2; m++) x[m] = pw_to<TC>(row[kk - 1 + m]);
 }
 
 template <typename TS, typename TC, int KV>
@@ -94,7 +91,7 @@ pw_adjoint_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__
     }
     const TC tcx = (TC)g.tcx, tcy = (TC)g.tcy;
     const bool active = (j < g.ny) && (kbase < g.nz);
-    const int nz = g.nz, nzl = g.nz - 1;  // zero at/above: u,v,gsu,gsv -> nz; w,gsw -> nz-1
+    const int nzl = g.nz - 1;
     const int nvalid = g.nz - kbase;
 
     int waited = 0;
@@ -128,7 +125,7 @@ pw_adjoint_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__
         // row offsets: j-1, j, j+1
         const int rS = tj * L, rC = (tj + 1) * L, rN = (tj + 2) * L;
         enum { U = 0, V = 1, W = 2, YU = 3, YV = 4, YW = 5 };
-#define COL(P, F, R, X) pw_adj_col<TS, TC, KV>((P) + (F) * fs + (R), kk, kbase, ((F) == W || (F) == YW) ? nzl : nz, X)
+#define COL(P, F, R, X) pw_adj_col<TS, TC, KV>((P) + (F) * fs + (R), kk, X)
         using TOut = TS;
         TOut ru[KV], rv[KV], rw[KV];
         {   // ---------------- gu ----------------
@@ -244,7 +241,8 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     if (smem > 227 * 1024) return pw_fail(PW_ERR_SHAPE, "adjoint tile needs %zu bytes of shared memory", smem);
     CUtensorMap maps[6];
     for (int q = 0; q < 6; q++) {
-        pw_status s = pw_make_field_map(&maps[q], in[q], m->dtype, m->nx, m->ny, m->nzp, g.kb, tile_j + 2);
+        pw_status s = pw_make_field_map(&maps[q], in[q], m->dtype, m->nx, m->ny, m->nzp, pw_kdim(m->nz, q % 3),
+                                        g.kb, tile_j + 2);
         if (s != PW_OK) return s;
     }
     auto kern = pw_adjoint_march<TS, TC, KV>;
@@ -280,6 +278,10 @@ static pw_status pw_adjoint_common(const pw_mesh *m, const void *u, const void *
     if (m->dtype != PW_F32 && m->dtype != PW_F64)
         return pw_fail(PW_ERR_DTYPE, "the adjoint is available for PW_F32 and PW_F64 meshes");
     cudaStream_t st = (cudaStream_t)stream;
+    if (m->nz == 1) {  // sw is identically 0 and w is all lid: gsw carries nothing
+        const size_t bytes = (size_t)m->total * pw_elem_in(m->dtype);
+        PW_CUDA(cudaMemsetAsync(gsw, 0, bytes, st));
+    }
     void *ys[3] = {gsu, gsv, gsw};
     pw_status s = pw_launch_halo(m, ys, 3, st);
     if (s != PW_OK) return s;

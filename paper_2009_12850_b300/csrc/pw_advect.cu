@@ -66,7 +66,8 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
     for (int q = 0; q < 3; q++) {
-        pw_status s = pw_make_field_map(&maps[q], f[q], m->dtype, m->nx, m->ny, m->nzp, g.kb, tile_j + 2);
+        pw_status s = pw_make_field_map(&maps[q], f[q], m->dtype, m->nx, m->ny, m->nzp, pw_kdim(m->nz, q),
+                                        g.kb, tile_j + 2);
         if (s != PW_OK) return s;
     }
     auto kern = pw_advect_march<TS, TC, TO, KV>;

@@ -9,9 +9,10 @@
 //
 // Layout of the work: the same x-march as the FP32 kernel.  A CTA owns tile_j
 // rows and a k chunk; TMA brings (j,k) planes of u, v, w (doubles) into a ring
-// of NS shared-memory slots; when a plane has landed, all threads convert it in
-// place, 16 bytes at a time, from (x_k, x_k+1) to (hi_k, hi_k+1, lo_k, lo_k+1),
-// zeroing the padding (k >= nz) and the w lid (k = nz-1) on the way.  Each
+// of NS shared-memory slots (levels >= nz and the w lid arrive as zeros: the
+// tensor maps carry the logical k extent); when a plane has landed, all threads
+// convert it in place, 16 bytes at a time, from (x_k, x_k+1) to
+// (hi_k, hi_k+1, lo_k, lo_k+1).  Each
 // thread then computes two levels (k, k+1) of one column per step.
 //
 // The algebra is the PW form regrouped around the face coefficients:
@@ -116,11 +117,8 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     auto conv_chunk = [&](double *base, int R, int q) {
         const int f = R / (TJ + 2), r = R - f * (TJ + 2);
         double *cp = base + (size_t)f * fs + (size_t)r * g.kb + 2 * q;
-        uint4 d = *reinterpret_cast<const uint4 *>(cp);  // (lo, hi) words of two doubles
-        const int klev = k0 - 2 + 2 * q;
-        const int kz = (f == 2) ? g.nz - 1 : g.nz;
-        if (klev >= kz) d.x = d.y = 0u;
-        if (klev + 1 >= kz) d.z = d.w = 0u;
+        // (lo, hi) words of two doubles; levels >= nz and the w lid arrived as 0
+        const uint4 d = *reinterpret_cast<const uint4 *>(cp);
         float h0, l0, h1, l1;
         split_words(d.x, d.y, h0, l0);
         split_words(d.z, d.w, h1, l1);
@@ -310,7 +308,8 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
     for (int q = 0; q < 3; q++) {
-        pw_status s = pw_make_field_map(&maps[q], f[q], PW_F64, m->nx, m->ny, m->nzp, g.kb, tile_j + 2);
+        pw_status s = pw_make_field_map(&maps[q], f[q], PW_F64, m->nx, m->ny, m->nzp, pw_kdim(m->nz, q), g.kb,
+                                        tile_j + 2);
         if (s != PW_OK) return s;
     }
     auto kern = tile_j == 4 ? (beta ? pw_advect_split_kernel<NS, 4, true> : pw_advect_split_kernel<NS, 4, false>)

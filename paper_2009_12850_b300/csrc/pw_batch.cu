@@ -193,7 +193,7 @@ static pw_status pw_batch_build(pw_batch_impl &b, cudaStream_t st) {
             M.sw = (float *)b.ptr[5][q];
             for (int f = 0; f < 3; f++) {
                 pw_status s2 = pw_make_field_map(&M.maps[f], b.ptr[f][q], PW_F32, m->nx, m->ny, m->nzp,
-                                                 M.g.kb, M.g.tj + 2);
+                                                 pw_kdim(m->nz, f), M.g.kb, M.g.tj + 2);
                 if (s2 != PW_OK) return s2;
             }
         }

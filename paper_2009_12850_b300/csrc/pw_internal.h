@@ -52,10 +52,13 @@ int pw_elem_in(pw_dtype d);    // bytes per field element
 int pw_elem_out(pw_dtype d);   // bytes per source element
 pw_status pw_check_ptr(const void *p, const char *name);
 
-// TMA descriptor for one field of a mesh: box {kbox, rows, 1} over
-// dims {nzp, ny+4, nx+4}.
+// TMA descriptor for one field of a mesh: box {kbox, rows, 1} over dims
+// {kdim, ny+4, nx+4} with row stride nzp elements.  kdim is the number of
+// levels the stencil may see: nz for u, v and their gradients, nz-1 for w and
+// its gradient (the lid reads as 0); at least 1.
 pw_status pw_make_field_map(CUtensorMap *map, const void *base, pw_dtype dtype, int nx, int ny,
-                            int nzp, int kbox, int rows);
+                            int nzp, int kdim, int kbox, int rows);
+static inline int pw_kdim(int nz, int field) { return field == 2 ? (nz > 1 ? nz - 1 : 1) : nz; }
 
 // launchers (pw_advect.cu / pw_adjoint.cu)
 pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const void *w,

@@ -140,14 +140,6 @@ __device__ __forceinline__ void pw_col_edges(const TS *row, int kk, TC (&x)[KV +
     }
 }
 
-// levels at or above kz read 0 (padding k >= nz; for w also the lid nz-1)
-template <typename TC, int KV>
-__device__ __forceinline__ void pw_zero_from(TC (&x)[KV + 2], int kbase, int kz) {
-#pragma unroll
-    for (int m = 0; m < KV + 2; m++)
-        if (kbase - 1 + m >= kz) x[m] = TC(0);
-}
-
 template <typename TC, int KV>
 __device__ __forceinline__ void pw_copy(TC (&d)[KV + 2], const TC (&s)[KV + 2]) {
 #pragma unroll
@@ -163,7 +155,9 @@ __device__ __forceinline__ void pw_copy(TC (&d)[KV + 2], const TC (&s)[KV + 2]) 
 // Register window along x: the centre-row columns of planes i-1 and i and the
 // side rows' values that the next step needs are carried in registers, so a
 // step loads only column i+1 of the centre row and the rows j-1, j+1 it still
-// lacks (9 slabs and 8 edge values instead of 17 slabs and 9 edges).
+// lacks (9 slabs and 8 edge values instead of 17 slabs and 9 edges).  Levels
+// at or above nz (and the w lid) arrive from TMA as zeros: the tensor maps
+// carry the logical k extent.
 // --------------------------------------------------------------------------
 template <typename TS, typename TC, typename TO, int KV, int NS>
 __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUtensorMap *mv_,
@@ -189,7 +183,6 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
     const bool in_tile = tj < g.tj;
     const int tjc = in_tile ? tj : g.tj - 1;  // rows read by threads outside the tile stay in the plane
     const bool active = in_tile && (j < g.ny) && (kbase < g.nz);
-    const bool top = kbase + KV >= g.nz - 1;  // slab touches the lid or the padding
     const int nvalid = g.nz - kbase;
     // shuffle partners: same column, same warp; lanes of a partial last warp
     const int wbase = tid & ~31;
@@ -244,7 +237,6 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
     const TC tcx = (TC)g.tcx, tcy = (TC)g.tcy;
     const int L = g.kb;
     const int rS = tjc * L, rC = (tjc + 1) * L, rN = (tjc + 2) * L;
-    const int zu = g.nz, zw = g.nz - 1;
 
     // the window: planes 0 (column i0-1) and 1 (column i0)
     TC uM[KV + 2], uC[KV + 2], vM[KV + 2], vC[KV + 2], wM[KV + 2], wC[KV + 2], vS[KV + 2], uNM[KV + 2];
@@ -263,16 +255,6 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
         pw_col_edges<TS, TC, KV>(P1 + 2 * fs + rC, kk, wC, mask, lo_shfl, hi_shfl, true, true);
         pw_col_edges<TS, TC, KV>(P1 + fs + rS, kk, vS, mask, lo_shfl, hi_shfl, false, true);
         pw_col_edges<TS, TC, KV>(P0 + rN, kk, uNM, mask, lo_shfl, hi_shfl, false, false);
-        if (top) {
-            pw_zero_from<TC, KV>(uM, kbase, zu);
-            pw_zero_from<TC, KV>(uC, kbase, zu);
-            pw_zero_from<TC, KV>(vM, kbase, zu);
-            pw_zero_from<TC, KV>(vC, kbase, zu);
-            pw_zero_from<TC, KV>(wM, kbase, zw);
-            pw_zero_from<TC, KV>(wC, kbase, zw);
-            pw_zero_from<TC, KV>(vS, kbase, zu);
-            pw_zero_from<TC, KV>(uNM, kbase, zu);
-        }
     }
 
     int waited = 2;
@@ -305,18 +287,6 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
         pw_col_edges<TS, TC, KV>(Pc + rN, kk, uN, mask, lo_shfl, hi_shfl, false, false);
         pw_col_edges<TS, TC, KV>(Pc + fs + rN, kk, vN, mask, lo_shfl, hi_shfl, false, false);
         pw_col_edges<TS, TC, KV>(Pc + 2 * fs + rN, kk, wN, mask, lo_shfl, hi_shfl, true, false);
-        if (top) {
-            pw_zero_from<TC, KV>(uP, kbase, zu);
-            pw_zero_from<TC, KV>(vP, kbase, zu);
-            pw_zero_from<TC, KV>(wP, kbase, zw);
-            pw_zero_from<TC, KV>(uS, kbase, zu);
-            pw_zero_from<TC, KV>(wS, kbase, zw);
-            pw_zero_from<TC, KV>(vSP, kbase, zu);
-            pw_zero_from<TC, KV>(uN, kbase, zu);
-            pw_zero_from<TC, KV>(vN, kbase, zu);
-            pw_zero_from<TC, KV>(wN, kbase, zw);
-        }
-
         if (active) {
             TO ru[KV], rv[KV], rw[KV];
 #pragma unroll

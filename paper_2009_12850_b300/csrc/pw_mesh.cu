@@ -78,14 +78,17 @@ static pw_encode_tiled_fn pw_encoder() {
 }
 
 pw_status pw_make_field_map(CUtensorMap *map, const void *base, pw_dtype dtype, int nx, int ny,
-                            int nzp, int kbox, int rows) {
+                            int nzp, int kdim, int kbox, int rows) {
     pw_encode_tiled_fn enc = pw_encoder();
     if (!enc) return pw_fail(PW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     int es = pw_elem_in(dtype);
     CUtensorMapDataType dt = dtype == PW_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                              : dtype == PW_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    cuuint64_t dims[3] = {(cuuint64_t)nzp, (cuuint64_t)(ny + 4), (cuuint64_t)(nx + 4)};
+    // the k extent is the logical one (nz, or nz-1 for w) while the row stride
+    // stays nzp: TMA fills levels beyond it with 0, which is how the padding and
+    // the lid face of w reach the stencil as zeros
+    cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)(ny + 4), (cuuint64_t)(nx + 4)};
     cuuint64_t strides[2] = {(cuuint64_t)nzp * es, (cuuint64_t)nzp * es * (ny + 4)};
     cuuint32_t box[3] = {(cuuint32_t)kbox, (cuuint32_t)rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
