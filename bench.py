@@ -47,24 +47,23 @@ def load_peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(sources):
+    """Hash of the files that define one kernel and its launch (paths relative
+    to the repository root)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2009_12850_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".h", ".cuh")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "pwadv.h"), "rb").read())
+    for name in sources:
+        h.update(open(os.path.join(ROOT, name), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel_key):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when the kernel sources changed since it was taken."""
+    summary, or None when that kernel's sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel_key)
-    if not d or d.get("source_hash") != kernel_source_hash():
+    if not d or d.get("source_hash") != kernel_source_hash(d.get("sources", [])):
         return None
     return d.get("bytes_per_launch")
 
