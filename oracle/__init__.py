@@ -48,6 +48,13 @@ def lib():
         L.pwo_euler.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_D] * 4 + [_D] * 3
                                 + [ctypes.c_double, ctypes.c_int])
         L.pwo_euler.restype = ctypes.c_int
+        L.pwo_scalar_coeffs.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, _D, _D]
+        L.pwo_scalar_coeffs.restype = None
+        L.pwo_scalar_src.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_D] * 2 + [_D] * 4 + [_D, _D]
+        L.pwo_scalar_src.restype = None
+        L.pwo_scalar_points.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_D] * 2 + [_D] * 4
+                                        + [ctypes.c_long, _L, _D, _D])
+        L.pwo_scalar_points.restype = None
         _lib = L
     return _lib
 
@@ -110,6 +117,13 @@ class Coeffs:
             setattr(self, n, arrs[n])
         self.tcx = 0.25 / self.dx
         self.tcy = 0.25 / self.dy
+        # scalar (theta, q) coefficients
+        self.rho0 = float(rho0)
+        self.hz1, self.hz2 = np.zeros(self.nz), np.zeros(self.nz)
+        lib().pwo_scalar_coeffs(self.nz, _p(self.dz), _p(self.rho_n), _p(self.rho_w), self.rho0,
+                                _p(self.hz1), _p(self.hz2))
+        self.hx = 0.5 / self.dx
+        self.hy = 0.5 / self.dy
 
     def args(self):
         return (self.tcx, self.tcy, _p(self.tzc1), _p(self.tzc2), _p(self.tzd1), _p(self.tzd2))
@@ -174,6 +188,32 @@ def adjoint_cond(c: Coeffs, u, v, w, gsu, gsv, gsw):
     lib().pwo_adjoint_mode(nx, ny, nz, *c.args(), _p(u), _p(v), _p(w), _p(gsu), _p(gsv), _p(gsw),
                            *[_p(x) for x in g], 0, 1)
     return tuple(g)
+
+
+def advect_scalar(c: Coeffs, u, v, w, phi, want_cond=False):
+    """PW source of the cell-centred scalar phi advected by (u, v, w)
+    (and its per-point condition sums if asked)."""
+    u, v, w, phi = _f64(u), _f64(v), _f64(w), _f64(phi)
+    nx, ny, nz = _shape(u)
+    assert nz == c.nz and phi.shape == u.shape
+    out = np.empty_like(u)
+    cond = np.empty_like(u) if want_cond else None
+    lib().pwo_scalar_src(nx, ny, nz, c.hx, c.hy, _p(c.hz1), _p(c.hz2), _p(u), _p(v), _p(w), _p(phi),
+                         _p(out), _p(cond))
+    return (out, cond) if want_cond else out
+
+
+def scalar_points(c: Coeffs, u, v, w, phi, pts):
+    """Scalar source at the given (n, 3) integer points; returns (values, cond), each (n,)."""
+    u, v, w, phi = _f64(u), _f64(v), _f64(w), _f64(phi)
+    nx, ny, nz = _shape(u)
+    pts = np.ascontiguousarray(pts, dtype=np.int64)
+    n = pts.shape[0]
+    out = np.empty(n)
+    cond = np.empty(n)
+    lib().pwo_scalar_points(nx, ny, nz, c.hx, c.hy, _p(c.hz1), _p(c.hz2), _p(u), _p(v), _p(w), _p(phi), n,
+                            pts.ctypes.data_as(_L), _p(out), _p(cond))
+    return out, cond
 
 
 def residual_sums(c: Coeffs, u, v, w, su, sv, sw):

@@ -511,3 +511,91 @@ int pwo_euler(int nx, int ny, int nz, double tcx, double tcy,
     free(s);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* scalars: theta and the moisture / tracer fields q                        */
+/* ------------------------------------------------------------------------ */
+/*
+ * Section 3 of the paper: the advection kernels serve every advected field;
+ * u, v and w are shared between them, and theta and the q fields are the
+ * further fields the device may be asked to advect.  A scalar phi sits at the
+ * cell centre (x_i, y_j, zn_k), so the six faces of its cell carry the wind
+ * components themselves: u(i-1,j,k) west and u(i,j,k) east, v(i,j-1,k) south
+ * and v(i,j,k) north, w(i,j,k-1) at the bottom (the ground when k = 0: w = 0)
+ * and w(i,j,k) at the top (the lid when k = nz-1: w = 0).  The PW skew form
+ * with these face velocities taken as they are (no averaging, so the
+ * coefficients are 0.5 where the momentum stencils have 0.25):
+ *   s = hx [u(i-1) phi(i-1) - u(i) phi(i+1)] + hy [v(j-1) phi(j-1) - v(j) phi(j+1)]
+ *     + hz1(k) w(k-1) phi(k-1) - hz2(k) w(k) phi(k+1)
+ *   hx = 0.5/dx, hy = 0.5/dy,
+ *   hz1(k) = 0.5 rho_w(k-1) / (rho_n(k) dz(k)),  hz2(k) = 0.5 rho_w(k) / (rho_n(k) dz(k)),
+ * with rho_w(-1) = rho0 (the ground face).
+ */
+void pwo_scalar_coeffs(int nz, const double *dz, const double *rhon, const double *rhow, double rho0,
+                       double *hz1, double *hz2)
+{
+    for (int k = 0; k < nz; k++) {
+        double rho_face_below = (k == 0) ? rho0 : rhow[k - 1];
+        hz1[k] = 0.5 * rho_face_below / (rhon[k] * dz[k]);
+        hz2[k] = 0.5 * rhow[k] / (rhon[k] * dz[k]);
+    }
+}
+
+static double src_scalar(const pwo_grid *g, const double *hz1, const double *hz2,
+                         const double *u, const double *v, const double *w, const double *p,
+                         long i, long j, long k, double *cond)
+{
+    long nz = g->nz;
+    double s, c;
+    s = g->tcx * (at(g, u, i - 1, j, k) * at(g, p, i - 1, j, k) - at(g, u, i, j, k) * at(g, p, i + 1, j, k));
+    c = fabs(g->tcx) * (fabs(at(g, u, i - 1, j, k)) * fabs(at(g, p, i - 1, j, k))
+                      + fabs(at(g, u, i, j, k)) * fabs(at(g, p, i + 1, j, k)));
+    s = s + g->tcy * (at(g, v, i, j - 1, k) * at(g, p, i, j - 1, k) - at(g, v, i, j, k) * at(g, p, i, j + 1, k));
+    c = c + fabs(g->tcy) * (fabs(at(g, v, i, j - 1, k)) * fabs(at(g, p, i, j - 1, k))
+                          + fabs(at(g, v, i, j, k)) * fabs(at(g, p, i, j + 1, k)));
+    if (k > 0) {            /* bottom face of cell 0 is the ground: w = 0 */
+        s = s + hz1[k] * at(g, w, i, j, k - 1) * at(g, p, i, j, k - 1);
+        c = c + fabs(hz1[k]) * fabs(at(g, w, i, j, k - 1)) * fabs(at(g, p, i, j, k - 1));
+    }
+    if (k < nz - 1) {       /* top face of cell nz-1 is the lid: w = 0 */
+        s = s - hz2[k] * at(g, w, i, j, k) * at(g, p, i, j, k + 1);
+        c = c + fabs(hz2[k]) * fabs(at(g, w, i, j, k)) * fabs(at(g, p, i, j, k + 1));
+    }
+    if (cond) *cond = c;
+    return s;
+}
+
+/* s (and optionally cond) = the PW source of the scalar phi advected by (u, v, w) */
+void pwo_scalar_src(int nx, int ny, int nz, double hx, double hy, const double *hz1, const double *hz2,
+                    const double *u, const double *v, const double *w, const double *phi,
+                    double *out, double *cond)
+{
+    pwo_grid g;
+    fill_grid(&g, nx, ny, nz, hx, hy, NULL, NULL, NULL, NULL);
+    long i;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (i = 0; i < nx; i++)
+        for (long j = 0; j < ny; j++)
+            for (long k = 0; k < nz; k++) {
+                size_t m = ((size_t)i * ny + j) * nz + k;
+                double c = 0.0;
+                out[m] = src_scalar(&g, hz1, hz2, u, v, w, phi, i, j, k, &c);
+                if (cond) cond[m] = c;
+            }
+}
+
+/* the scalar source at a list of points (n triples i, j, k) */
+void pwo_scalar_points(int nx, int ny, int nz, double hx, double hy, const double *hz1, const double *hz2,
+                       const double *u, const double *v, const double *w, const double *phi,
+                       long n, const long *pts, double *out, double *cond)
+{
+    pwo_grid g;
+    fill_grid(&g, nx, ny, nz, hx, hy, NULL, NULL, NULL, NULL);
+    for (long p = 0; p < n; p++) {
+        double c = 0.0;
+        out[p] = src_scalar(&g, hz1, hz2, u, v, w, phi, pts[3 * p], pts[3 * p + 1], pts[3 * p + 2], &c);
+        if (cond) cond[p] = c;
+    }
+}

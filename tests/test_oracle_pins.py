@@ -326,9 +326,158 @@ def pin_lid_ignored():
         assert np.array_equal(a, b)
 
 
+# --------------------------------------------------------------------------
+# scalars (theta, q): the cell-centred form
+# --------------------------------------------------------------------------
+def pin_scalar_worked_examples():
+    spec = json.load(open(os.path.join(GOLDEN, "pw_scalar_worked_examples.json")))
+    ex = {e["name"]: e["expect"] for e in spec["examples"]}
+    c = unit_coeffs()
+    I, J, K = grid_idx()
+    z = np.zeros((4, 4, 4))
+    s = oracle.advect_scalar(c, 1.0 + z, z, z, 1.0 * I)
+    np.testing.assert_array_equal(s, np.broadcast_to(np.array(ex["S1"]["s_i"])[:, None, None], s.shape))
+    w = np.broadcast_to(np.array([1.0, 2.0, 1.0, 0.0]), (4, 4, 4)).copy()
+    s = oracle.advect_scalar(c, z, z, w, 1.0 * K)
+    np.testing.assert_array_equal(s, np.broadcast_to(np.array(ex["S2"]["s_k"]), s.shape))
+    s = oracle.advect_scalar(c, z, 1.0 + J, z, 1.0 + z)
+    np.testing.assert_array_equal(s, np.broadcast_to(np.array(ex["S3"]["s_j"])[None, :, None], s.shape))
+    s = oracle.advect_scalar(c, 1.0 + J, 2.0 + z, z, 1.0 * (I + J))
+    np.testing.assert_array_equal(s, np.broadcast_to(np.array(ex["S4"]["s_ij"])[:, :, None], s.shape))
+    # stretched, stratified column: a unit spike of phi at level k0 under w = 1
+    # gives hz1(k0+1) one level up and -hz2(k0-1) one level down
+    co = spec["coefficients_nz3"]
+    c3 = oracle.Coeffs(3, co["dx"], co["dx"])
+    hz1 = [a * math.exp(e / 8000.0) for a, e in co["hz1"]]
+    hz2 = [a * math.exp(e / 8000.0) for a, e in co["hz2"]]
+    assert c3.hx == co["hx"] and c3.hy == co["hx"]
+    np.testing.assert_allclose(c3.hz1, hz1, rtol=2e-15, atol=0)
+    np.testing.assert_allclose(c3.hz2, hz2, rtol=2e-15, atol=0)
+    one = np.ones((3, 3, 3))
+    w = one.copy()
+    w[:, :, -1] = 0.0
+    for k0 in range(3):
+        phi = np.zeros((3, 3, 3))
+        phi[:, :, k0] = 1.0
+        s = oracle.advect_scalar(c3, 0 * one, 0 * one, w, phi)
+        col = s[1, 2]
+        if k0 + 1 < 3:
+            assert abs(col[k0 + 1] - hz1[k0 + 1]) <= 2e-15 * hz1[k0 + 1], (k0, col)
+        if k0 >= 1:
+            assert abs(col[k0 - 1] + hz2[k0 - 1]) <= 2e-15 * hz2[k0 - 1], (k0, col)
+        assert col[k0] == 0.0
+
+
+def pin_scalar_uniform_and_centred():
+    rng = np.random.default_rng(21)
+    nx, ny, nz, dx, dy = 6, 5, 7, 31.0, 17.0
+    c = oracle.Coeffs(nz, dx, dy, dz=rng.uniform(5, 50, nz), rho_n=rng.uniform(0.5, 1.5, nz),
+                      rho_w=rng.uniform(0.5, 1.5, nz))
+    U, V, W = np.full((nx, ny, nz), 7.25), np.full((nx, ny, nz), -3.5), np.zeros((nx, ny, nz))
+    assert not oracle.advect_scalar(c, U, V, W, np.full((nx, ny, nz), 2.5)).any()
+    # constant horizontal wind: minus the centred advective derivative
+    phi = rng.standard_normal((nx, ny, nz))
+    s = oracle.advect_scalar(c, U, V, W, phi)
+    want = (-7.25 * (np.roll(phi, -1, 0) - np.roll(phi, 1, 0)) / (2 * dx)
+            + 3.5 * (np.roll(phi, -1, 1) - np.roll(phi, 1, 1)) / (2 * dy))
+    np.testing.assert_allclose(s, want, rtol=0, atol=1e-14 * np.abs(want).max())
+
+
+def pin_scalar_energy_and_skew():
+    rng = np.random.default_rng(22)
+    for nx, ny, nz in ((7, 5, 6), (4, 9, 2), (3, 3, 1)):
+        c = stretched(nz)
+        u, v, w = rand_fields(rng, nx, ny, nz)
+        phi, psi = rng.standard_normal((2, nx, ny, nz)) + 290.0
+        s, cond = oracle.advect_scalar(c, u, v, w, phi, want_cond=True)
+        assert np.all(np.abs(s) <= cond * (1 + 1e-15))
+        num, den = wdot(c, phi, s, 0), wdot(c, np.abs(phi), np.abs(s), 0)
+        assert abs(num) <= 1e-14 * den + 1e-300, (num, den)
+        lhs = wdot(c, psi, s, 0)
+        rhs = -wdot(c, oracle.advect_scalar(c, u, v, w, psi), phi, 0)
+        assert abs(lhs - rhs) <= 1e-13 * wdot(c, np.abs(psi), np.abs(s), 0), (lhs, rhs)
+
+
+def pin_scalar_divergence_identity():
+    """Summation by parts: sum W s = 1/2 sum W phi D with D the anelastic
+    divergence of the cell's face fluxes (written out here, not by the oracle)."""
+    rng = np.random.default_rng(23)
+    nx, ny, nz, dx, dy = 7, 6, 8, 37.0, 53.0
+    c = stretched(nz, dx, dy)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    phi = 300.0 + rng.standard_normal((nx, ny, nz))
+    s = oracle.advect_scalar(c, u, v, w, phi)
+    fw = c.rho_w[None, None, :] * w
+    fw[:, :, -1] = 0.0                                   # lid
+    below = np.concatenate([np.zeros((nx, ny, 1)), fw[:, :, :-1]], axis=2)   # ground
+    D = ((u - np.roll(u, 1, 0)) / dx + (v - np.roll(v, 1, 1)) / dy
+         + (fw - below) / (c.rho_n * c.dz)[None, None, :])
+    lhs = wdot(c, np.ones_like(s), s, 0)
+    rhs = 0.5 * wdot(c, phi, D, 0)
+    scale = wdot(c, np.ones_like(s), np.abs(s), 0)
+    assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs)
+    assert abs(lhs) > 1e-6 * scale
+    # a discretely divergence-free wind conserves every scalar
+    x = streamfunction_flow(rng, nx, ny, nz, dx, dy)
+    s = oracle.advect_scalar(c, *x, phi)
+    assert abs(wdot(c, np.ones_like(s), s, 0)) <= 1e-14 * wdot(c, np.ones_like(s), np.abs(s), 0)
+
+
+def pin_scalar_continuum_second_order():
+    import sympy as sp
+    H = 1500.0
+    x, y, zz = sp.symbols("x y z", real=True)
+    Lx, Ly, Z = 2000.0, 1600.0, 1000.0
+    kx, ky = 2 * sp.pi / Lx, 2 * sp.pi / Ly
+    u = 3 + sp.sin(kx * x + 0.4) * sp.cos(ky * y) * (1 + 0.3 * sp.cos(sp.pi * zz / Z))
+    v = 2 + sp.cos(kx * x) * sp.sin(ky * y + 0.7) * (1 + 0.2 * zz / Z)
+    w = 0.5 * sp.sin(sp.pi * zz / Z) * sp.cos(kx * x + 0.1) * sp.sin(ky * y + 0.2)
+    th = 300 + 2 * sp.cos(kx * x + 0.3) * sp.sin(ky * y + 1.1) + 5 * sp.sin(sp.pi * zz / (2 * Z))
+    rho = 1.2 * sp.exp(-zz / H)
+    div = (sp.diff(rho * u, x) + sp.diff(rho * v, y) + sp.diff(rho * w, zz)) / rho
+    S = -(u * sp.diff(th, x) + v * sp.diff(th, y) + w * sp.diff(th, zz)) - th * div / 2
+    fl = [sp.lambdify((x, y, zz), f, "numpy") for f in (u, v, w, th)]
+    Sl = sp.lambdify((x, y, zz), S, "numpy")
+    errs = []
+    for N in (12, 24, 48):
+        dx, dy, dz = Lx / N, Ly / N, Z / N
+        c = oracle.Coeffs(N, dx, dy, dz=np.full(N, dz), rho0=1.2, H=H)
+        i = np.arange(N)[:, None, None]
+        j = np.arange(N)[None, :, None]
+        zn = ((np.arange(N) + 0.5) * dz)[None, None, :]
+        zf = ((np.arange(N) + 1.0) * dz)[None, None, :]
+        pts = [((i + 0.5) * dx, j * dy, zn), (i * dx, (j + 0.5) * dy, zn), (i * dx, j * dy, zf),
+               (i * dx, j * dy, zn)]
+        F = [np.broadcast_to(fl[q](*pts[q]), (N, N, N)).astype(np.float64).copy() for q in range(4)]
+        F[2][:, :, -1] = 0.0
+        s = oracle.advect_scalar(c, *F)
+        ref = np.broadcast_to(Sl(*pts[3]), (N, N, N))
+        errs.append(float(np.abs(s - ref).max() / np.abs(ref).max()))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.3 < r1 < 4.8 and 3.3 < r2 < 4.8, errs
+
+
+def pin_scalar_lid_and_points():
+    rng = np.random.default_rng(24)
+    nx, ny, nz = 5, 4, 6
+    c = stretched(nz)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    phi = rng.standard_normal((nx, ny, nz))
+    w2 = w.copy()
+    w2[:, :, -1] = 100.0 * rng.standard_normal((nx, ny))
+    s, cond = oracle.advect_scalar(c, u, v, w, phi, want_cond=True)
+    assert np.array_equal(s, oracle.advect_scalar(c, u, v, w2, phi))
+    pts = np.array([[0, 0, 0], [4, 3, 5], [2, 1, 0], [1, 0, 5], [3, 2, 3]])
+    vals, cv = oracle.scalar_points(c, u, v, w, phi, pts)
+    for p, (i, j, k) in enumerate(pts):
+        assert vals[p] == s[i, j, k] and cv[p] == cond[i, j, k]
+
+
 PINS = [pin_worked_examples, pin_lid_ignored, pin_coefficients, pin_uniform_flow, pin_energy, pin_skew_adjoint,
         pin_momentum_divergence_free, pin_momentum_identity, pin_continuum_second_order,
-        pin_adjoint_dot, pin_adjoint_bruteforce, pin_cond_and_points]
+        pin_adjoint_dot, pin_adjoint_bruteforce, pin_cond_and_points,
+        pin_scalar_worked_examples, pin_scalar_uniform_and_centred, pin_scalar_energy_and_skew,
+        pin_scalar_divergence_identity, pin_scalar_continuum_second_order, pin_scalar_lid_and_points]
 
 
 @pytest.mark.parametrize("pin", PINS + [pin_loop_gradient], ids=lambda f: f.__name__)
@@ -390,6 +539,20 @@ MUTANTS = {
                          "        else dz[k] = 10.0 * pow(4.0, (double)k / (double)nz);"),
     "dzn_offset": ("    for (int k = 0; k < nz; k++) dzn[k] = (k < nz - 1) ? zn[k + 1] - zn[k] : 0.0;",
                    "    for (int k = 0; k < nz; k++) dzn[k] = (k < nz - 1) ? zf[k + 1] - zf[k] : 0.0;"),
+    "scalar_x_sign": ("* at(g, p, i - 1, j, k) - at(g, u, i, j, k) * at(g, p, i + 1, j, k));",
+                      "* at(g, p, i - 1, j, k) + at(g, u, i, j, k) * at(g, p, i + 1, j, k));"),
+    "scalar_y_face": ("    s = s + g->tcy * (at(g, v, i, j - 1, k) * at(g, p, i, j - 1, k)",
+                      "    s = s + g->tcy * (at(g, v, i, j, k) * at(g, p, i, j - 1, k)"),
+    "scalar_drop_top": ("        s = s - hz2[k] * at(g, w, i, j, k) * at(g, p, i, j, k + 1);",
+                        "        s = s;"),
+    "scalar_bottom_level": ("        s = s + hz1[k] * at(g, w, i, j, k - 1) * at(g, p, i, j, k - 1);",
+                            "        s = s + hz1[k] * at(g, w, i, j, k) * at(g, p, i, j, k - 1);"),
+    "scalar_hz1_rho": ("        hz1[k] = 0.5 * rho_face_below / (rhon[k] * dz[k]);",
+                       "        hz1[k] = 0.5 * rhow[k] / (rhon[k] * dz[k]);"),
+    "scalar_ground_density": ("        double rho_face_below = (k == 0) ? rho0 : rhow[k - 1];",
+                              "        double rho_face_below = (k == 0) ? rhon[0] : rhow[k - 1];"),
+    "scalar_quarter_width": ("        hz2[k] = 0.5 * rhow[k] / (rhon[k] * dz[k]);",
+                             "        hz2[k] = 0.25 * rhow[k] / (rhon[k] * dz[k]);"),
 }
 
 
