@@ -177,6 +177,28 @@ pw_status pw_halo_fold(const pw_mesh *mesh, void *f1, void *f2, void *f3, void *
 pw_status pw_advect(const pw_mesh *mesh, const void *u, const void *v, const void *w,
                     void *su, void *sv, void *sw, int beta, void *stream);
 
+/* Most scalars one pw_advect_scalars call advects. */
+#define PW_MAX_SCALARS 16
+
+/* PW advection of n cell-centred scalars (theta and the moisture / tracer
+ * fields q: the further fields the advection component serves with the same
+ * wind, section 3).  A scalar sits at the cell centre, so the wind on each face
+ * of its cell is used as it is:
+ *  s = hx [u(i-1) phi(i-1) - u(i) phi(i+1)] + hy [v(j-1) phi(j-1) - v(j) phi(j+1)]
+ *    + hz1(k) w(k-1) phi(k-1) - hz2(k) w(k) phi(k+1)
+ * with hx = 0.5/dx, hy = 0.5/dy, hz1(k) = 0.5 rho_w(k-1)/(rho_n(k) dz(k)),
+ * hz2(k) = 0.5 rho_w(k)/(rho_n(k) dz(k)) (twice the momentum coefficients
+ * tcx, tcy, tzc1, tzc2), w(-1) = 0 at the ground and w(nz-1) = 0 at the lid
+ * (never read).  phi and sphi are HOST arrays of n device pointers (1 <= n <=
+ * PW_MAX_SCALARS): phi[a] is a field of the mesh dtype and layout with its
+ * halos filled (pw_halo_periodic), sphi[a] its source, binary64 for PW_F64 and
+ * binary32 otherwise; beta as in pw_advect.  Halos of u, v, w must be filled.
+ * The wind is read once per group of scalars that fits a CTA's shared memory.
+ * FP64 meshes compute in native FP64 arithmetic.  No output may alias an input
+ * or another output. */
+pw_status pw_advect_scalars(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
+                            const void *const *phi, void *const *sphi, int beta, void *stream);
+
 /* Adjoint (transpose of the Jacobian of the map (u,v,w) -> (su,sv,sw) at the
  * given u, v, w) applied to incoming gradients gsu, gsv, gsw, with the periodic
  * halo fold included: gu, gv, gw receive gradients with respect to the INTERIOR

@@ -16,6 +16,7 @@ PW_ERR_LID, PW_ERR_CUDA, PW_ERR_TIMEOUT, PW_ERR_NOMEM, PW_ERR_IO = -5, -6, -7, -
 PW_F64, PW_F32, PW_BF16 = 0, 1, 2
 PW_ALGO_AUTO, PW_ALGO_F64_NATIVE, PW_ALGO_F64_SPLIT = 0, 1, 2
 PW_NOALLOC_MAX_NZ = 4096
+PW_MAX_SCALARS = 16
 
 
 class pw_mesh_desc(ctypes.Structure):
@@ -58,6 +59,7 @@ _SIGS = {
     "pw_halo_periodic": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_halo_fold": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_advect": ([_vp] + [_vp] * 6 + [_i, _vp], _i),
+    "pw_advect_scalars": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp], _i),
     "pw_advect_adjoint": ([_vp] + [_vp] * 9 + [_d, _i, _vp], _i),
     "pw_euler_adjoint": ([_vp] + [_vp] * 9 + [_d, _vp], _i),
     "pw_euler": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
@@ -160,6 +162,12 @@ def pw_halo_fold(mesh, f1, f2, f3, stream):
 
 def pw_advect(mesh, u, v, w, su, sv, sw, beta, stream):
     check(_c.pw_advect(mesh, u, v, w, su, sv, sw, int(beta), stream), "pw_advect")
+
+
+def pw_advect_scalars(mesh, u, v, w, phi, sphi, beta, stream):
+    """phi, sphi: sequences of device pointers (one per scalar)."""
+    check(_c.pw_advect_scalars(mesh, u, v, w, len(phi), _ptrs(phi), _ptrs(sphi), int(beta), stream),
+          "pw_advect_scalars")
 
 
 def pw_advect_adjoint(mesh, u, v, w, gsu, gsv, gsw, gu, gv, gw, alpha, beta, stream):

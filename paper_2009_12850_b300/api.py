@@ -128,6 +128,18 @@ class Mesh:
                     beta, _stream(stream))
         return su, sv, sw
 
+    def advect_scalars(self, u, v, w, phis, sources=None, beta=0, stream=None):
+        """PW sources of the cell-centred scalars phis (list of field tensors
+        with halos filled) advected by (u, v, w); returns the list of sources."""
+        phis = list(phis)
+        sources = [self.empty_out() for _ in phis] if sources is None else list(sources)
+        if len(sources) != len(phis):
+            raise ValueError("one source tensor per scalar")
+        L.pw_advect_scalars(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                            [self._check(p, "phi") for p in phis],
+                            [self._check(s, "sphi", True) for s in sources], beta, _stream(stream))
+        return sources
+
     def adjoint(self, u, v, w, gsu, gsv, gsw, gu=None, gv=None, gw=None, alpha=1.0, beta=0, stream=None):
         gu = self.zeros() if gu is None else gu
         gv = self.zeros() if gv is None else gv

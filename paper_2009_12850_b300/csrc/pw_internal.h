@@ -64,6 +64,9 @@ static inline int pw_kdim(int nz, int field) { return field == 2 ? (nz > 1 ? nz 
 pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const void *w,
                            void *su, void *sv, void *sw, int beta, cudaStream_t st,
                            int tile_j, int tile_i);
+pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
+                                   const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
+                                   int tile_j, int tile_i, int group);
 pw_status pw_launch_halo(const pw_mesh *m, void *const *f, int nf, cudaStream_t st);
 pw_status pw_launch_residuals_raw(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
                                   const double *ww, const void *u, const void *v, const void *w,

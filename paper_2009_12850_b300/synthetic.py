@@ -76,6 +76,19 @@ def shear_fields(nx, ny, nz, seed, top_speed=15.0, noise=2.0, w_std=0.3, dz=None
     return u, v, w
 
 
+def scalar_fields(nx, ny, nz, n, seed, dz=None):
+    """n cell-centred scalars: theta (K) first, then n - 1 moisture / tracer
+    fields (kg/kg).  theta = 300 + 0.003 z + N(0, 0.5) (a stably stratified
+    column with warm and cold perturbations); q_m = 1e-3 (m + 1) U(0, 1)."""
+    dz = default_dz(nz) if dz is None else np.asarray(dz, dtype=np.float64)
+    centre = np.cumsum(dz) - 0.5 * dz
+    rng = np.random.default_rng(seed)
+    out = [300.0 + 0.003 * centre[None, None, :] + 0.5 * rng.standard_normal((nx, ny, nz))]
+    for m in range(1, n):
+        out.append(1e-3 * (m + 1) * rng.random((nx, ny, nz)))
+    return out
+
+
 def fields_for(wl: Workload):
     if wl.kind == "shear":
         return shear_fields(wl.nx, wl.ny, wl.nz, wl.seed)

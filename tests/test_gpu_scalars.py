@@ -1,0 +1,190 @@
+"""GPU parity of the scalar (theta, q) PW advection through the C-ABI against the
+FP64 oracle: FP64 (native FP64 arithmetic), FP32 and BF16 storage, ragged
+shapes, grouping of many scalars, accumulation, argument checks, and sampled
+points of a full 1024x1024x128 launch."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_12850_b300 import synthetic
+
+from parity import TOL_F32_COND, TOL_F64, compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pw():
+    from paper_2009_12850_b300 import build
+    build.build()
+    from paper_2009_12850_b300 import api
+    return api
+
+
+def rounded(arrs, dtype):
+    t = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(t).to(torch.float64).numpy() for a in arrs]
+
+
+def run_scalars(pw, m, wind, phis, beta=0, init=None):
+    U = [m.from_interior(a) for a in wind]
+    P = [m.from_interior(a) for a in phis]
+    S = [m.empty_out() for _ in phis]
+    if init is not None:
+        for s, a in zip(S, init):
+            s.zero_()
+            m.interior(s).copy_(torch.from_numpy(a).to(s.dtype))
+    m.advect_scalars(*U, P, S, beta=beta)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    return [m.interior(s).double().cpu().numpy() for s in S]
+
+
+def tolerances(dtype):
+    return (TOL_F64, TOL_F64) if dtype == "f64" else (TOL_F32_COND, TOL_F32_COND)
+
+
+SHAPES = [(64, 64, 64), (37, 23, 13), (5, 7, 1), (1, 9, 6), (9, 1, 5), (3, 3, 2), (50, 17, 130),
+          (16, 24, 300)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_scalars_match_oracle(pw, shape, dtype):
+    nx, ny, nz = shape
+    m = pw.Mesh(nx, ny, nz, 50.0, 35.0, dtype=dtype)
+    wind = rounded(synthetic.wind_fields(nx, ny, nz, 11), dtype)
+    phis = rounded(synthetic.scalar_fields(nx, ny, nz, 3, 12), dtype)
+    got = run_scalars(pw, m, wind, phis)
+    c = oracle.Coeffs(nz, 50.0, 35.0)
+    tn, tc = tolerances(dtype)
+    for q, phi in enumerate(phis):
+        ref, cond = oracle.advect_scalar(c, *wind, phi, want_cond=True)
+        compare(f"s{q}", got[q], ref, cond, tn, tc)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 16])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_scalar_counts_and_groups(pw, n, dtype):
+    nx, ny, nz = 21, 34, 70
+    m = pw.Mesh(nx, ny, nz, 40.0, dtype=dtype)
+    wind = rounded(synthetic.wind_fields(nx, ny, nz, 13), dtype)
+    phis = rounded(synthetic.scalar_fields(nx, ny, nz, n, 14), dtype)
+    got = run_scalars(pw, m, wind, phis)
+    c = oracle.Coeffs(nz, 40.0, 40.0)
+    tn, tc = tolerances(dtype)
+    for q, phi in enumerate(phis):
+        ref, cond = oracle.advect_scalar(c, *wind, phi, want_cond=True)
+        compare(f"s{q}", got[q], ref, cond, tn, tc)
+
+
+@pytest.mark.parametrize("tile", [(1, 16), (2, 7), (4, 64), (8, 32), (3, 200)])
+def test_scalar_tiles_do_not_change_results(pw, tile):
+    nx, ny, nz = 45, 29, 40
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64")
+    wind = synthetic.wind_fields(nx, ny, nz, 15)
+    phis = synthetic.scalar_fields(nx, ny, nz, 4, 16)
+    base = run_scalars(pw, m, wind, phis)
+    m.set_tile(*tile)
+    other = run_scalars(pw, m, wind, phis)
+    for a, b in zip(base, other):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_scalar_accumulate(pw, dtype):
+    nx, ny, nz = 19, 22, 17
+    m = pw.Mesh(nx, ny, nz, 30.0, dtype=dtype)
+    wind = rounded(synthetic.wind_fields(nx, ny, nz, 17), dtype)
+    phis = rounded(synthetic.scalar_fields(nx, ny, nz, 2, 18), dtype)
+    rng = np.random.default_rng(19)
+    init = [rng.standard_normal((nx, ny, nz)) for _ in phis]
+    init = rounded(init, dtype)
+    got = run_scalars(pw, m, wind, phis, beta=1, init=init)
+    c = oracle.Coeffs(nz, 30.0, 30.0)
+    tn, tc = tolerances(dtype)
+    for q, phi in enumerate(phis):
+        ref, cond = oracle.advect_scalar(c, *wind, phi, want_cond=True)
+        compare(f"s{q}", got[q], ref + init[q], cond + np.abs(init[q]), 2 * tn, 2 * tc)
+
+
+def test_scalar_uniform_and_lid(pw):
+    nx, ny, nz = 12, 10, 9
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64")
+    U, V, W = np.full((nx, ny, nz), 4.0), np.full((nx, ny, nz), -2.0), np.zeros((nx, ny, nz))
+    got = run_scalars(pw, m, (U, V, W), [np.full((nx, ny, nz), 301.5)])
+    assert not got[0].any()
+    wind = list(synthetic.wind_fields(nx, ny, nz, 20))
+    phis = synthetic.scalar_fields(nx, ny, nz, 1, 21)
+    a = run_scalars(pw, m, wind, phis)
+    wind[2] = wind[2].copy()
+    wind[2][:, :, -1] = 1e3
+    b = run_scalars(pw, m, wind, phis)
+    assert np.array_equal(a[0], b[0])
+
+
+def test_scalar_outputs_untouched_outside_interior(pw):
+    nx, ny, nz = 9, 8, 7
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f32")
+    wind = synthetic.wind_fields(nx, ny, nz, 22)
+    phis = synthetic.scalar_fields(nx, ny, nz, 2, 23)
+    U = [m.from_interior(a) for a in wind]
+    P = [m.from_interior(a) for a in phis]
+    S = [torch.full(m.shape, 7.0, dtype=torch.float32, device=m.device) for _ in phis]
+    m.advect_scalars(*U, P, S)
+    torch.cuda.synchronize()
+    for s in S:
+        mask = torch.ones(m.shape, dtype=torch.bool, device=m.device)
+        mask[2:nx + 2, 2:ny + 2, :nz] = False
+        assert torch.all(s[mask] == 7.0)
+
+
+def test_scalar_argument_errors(pw):
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz = 8, 8, 8
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f32")
+    U = [m.zeros() for _ in range(3)]
+    P = [m.zeros() for _ in range(17)]
+    S = [m.empty_out() for _ in range(17)]
+    with pytest.raises(L.PWError):
+        m.advect_scalars(*U, P, S)                       # 17 > PW_MAX_SCALARS
+    with pytest.raises(L.PWError):
+        m.advect_scalars(*U, [], [])                     # none
+    with pytest.raises(L.PWError):
+        m.advect_scalars(*U, P[:2], [S[0], S[0]])        # outputs alias
+    with pytest.raises(L.PWError):
+        m.advect_scalars(*U, P[:1], [U[0]])              # output aliases the wind
+    with pytest.raises(L.PWError):
+        m.advect_scalars(*U, P[:2], [P[1], S[0]])        # output aliases a scalar
+    with pytest.raises(L.PWError):
+        m.advect_scalars(*U, P[:1], S[:1], beta=2)
+    assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_scalars_full_size_sampled(pw, dtype):
+    """1024x1024x128 (the bandwidth workload), two scalars, the default launch:
+    every sampled output against the oracle evaluated point by point."""
+    wl = synthetic.LARGE
+    nx, ny, nz = wl.nx, wl.ny, wl.nz
+    m = pw.Mesh(nx, ny, nz, wl.dx, wl.dy, dtype=dtype)
+    wind = rounded(synthetic.fields_for(wl), dtype)
+    phis = rounded(synthetic.scalar_fields(nx, ny, nz, 2, wl.seed + 100), dtype)
+    U = [m.from_interior(a) for a in wind]
+    P = [m.from_interior(a) for a in phis]
+    S = m.advect_scalars(*U, P)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    rng = np.random.default_rng(24)
+    pts = np.stack([rng.integers(0, nx, 4000), rng.integers(0, ny, 4000), rng.integers(0, nz, 4000)], 1)
+    edges = np.array([[0, 0, 0], [nx - 1, ny - 1, nz - 1], [0, ny - 1, nz - 1], [nx - 1, 0, 0],
+                      [5, 7, nz - 1], [nx - 1, 3, 64], [2, ny - 1, 63]])
+    pts = np.concatenate([pts, edges])
+    c = oracle.Coeffs(nz, wl.dx, wl.dy)
+    tn, tc = tolerances(dtype)
+    idx = torch.from_numpy(pts).to(m.device)
+    for q, phi in enumerate(phis):
+        ref, cond = oracle.scalar_points(c, *wind, phi, pts)
+        got = m.interior(S[q])[idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+        compare(f"s{q}", got, ref, cond, tn, tc)
