@@ -194,8 +194,10 @@ pw_status pw_advect(const pw_mesh *mesh, const void *u, const void *v, const voi
  * halos filled (pw_halo_periodic), sphi[a] its source, binary64 for PW_F64 and
  * binary32 otherwise; beta as in pw_advect.  Halos of u, v, w must be filled.
  * The wind is read once per group of scalars that fits a CTA's shared memory.
- * FP64 meshes compute in native FP64 arithmetic.  No output may alias an input
- * or another output. */
+ * FP64 meshes compute in double-float arithmetic on the FP32 pipe (algo
+ * PW_ALGO_F64_SPLIT, the default; same accuracy contract as pw_advect) or in
+ * native FP64 (PW_ALGO_F64_NATIVE).  No output may alias an input or another
+ * output. */
 pw_status pw_advect_scalars(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
                             const void *const *phi, void *const *sphi, int beta, void *stream);
 

@@ -138,3 +138,27 @@ __device__ __forceinline__ double join(float hi, float lo) {
     const double d = widen_normal(hi) + widen_normal(lo);
     return (hi == 0.0f && lo == 0.0f) ? 0.0 : d;
 }
+
+// ---------------------------------------------------------------------------
+// access to the split stencils' tables and converted planes
+// ---------------------------------------------------------------------------
+// coefficient table (floats): 8 arrays of cs_n levels starting at level -2:
+// g_h g_l gp_h gp_l r_h r_l rp_h rp_l, then tcx_h tcx_l tcy_h tcy_l
+__device__ __forceinline__ D2 cs_pair(const float *cs, int n, int arr, int k) {
+    const float *h = cs + (2 * arr) * n + k + 2;
+    const float *l = cs + (2 * arr + 1) * n + k + 2;
+    return D2{pk(h[0], h[1]), pk(l[0], l[1])};
+}
+
+// D2 of levels (k+s, k+1+s), s in {-1, 0, 1}, from a converted plane row
+template <int S>
+__device__ __forceinline__ D2 ld2(const double *row, int kk) {
+    const float4 c = *reinterpret_cast<const float4 *>(row + kk);
+    if (S == 0) return D2{pk(c.x, c.y), pk(c.z, c.w)};
+    if (S < 0) {
+        const float4 m = *reinterpret_cast<const float4 *>(row + kk - 2);
+        return D2{pk(m.y, c.x), pk(m.w, c.z)};
+    }
+    const float4 p = *reinterpret_cast<const float4 *>(row + kk + 2);
+    return D2{pk(c.y, p.x), pk(c.w, p.z)};
+}

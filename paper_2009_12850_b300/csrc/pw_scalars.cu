@@ -314,11 +314,17 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     return PW_OK;
 }
 
+pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
+                                  const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
+                                  int tile_j, int tile_i, int group);
+
 pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
                                    const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
                                    int tile_j, int tile_i, int group) {
     switch (m->dtype) {
         case PW_F64:
+            if (m->algo == PW_ALGO_F64_SPLIT)
+                return pw_launch_scalars_split(m, u, v, w, n, phi, sphi, beta, st, tile_j, tile_i, group);
             return pw_launch_scalars<double, double, double, 2>(m, u, v, w, n, phi, sphi, beta, st, tile_j,
                                                                 tile_i, group);
         case PW_F32:

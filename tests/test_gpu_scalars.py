@@ -1,5 +1,5 @@
 """GPU parity of the scalar (theta, q) PW advection through the C-ABI against the
-FP64 oracle: FP64 (native FP64 arithmetic), FP32 and BF16 storage, ragged
+FP64 oracle: FP64 (double-float split and native FP64), FP32 and BF16 storage, ragged
 shapes, grouping of many scalars, accumulation, argument checks, and sampled
 points of a full 1024x1024x128 launch."""
 import numpy as np
@@ -49,11 +49,14 @@ SHAPES = [(64, 64, 64), (37, 23, 13), (5, 7, 1), (1, 9, 6), (9, 1, 5), (3, 3, 2)
           (16, 24, 300)]
 
 
+KINDS = [("f64", "split"), ("f64", "native"), ("f32", "auto"), ("bf16", "auto")]
+
+
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
-def test_scalars_match_oracle(pw, shape, dtype):
+@pytest.mark.parametrize("dtype,algo", KINDS)
+def test_scalars_match_oracle(pw, shape, dtype, algo):
     nx, ny, nz = shape
-    m = pw.Mesh(nx, ny, nz, 50.0, 35.0, dtype=dtype)
+    m = pw.Mesh(nx, ny, nz, 50.0, 35.0, dtype=dtype, algo=algo)
     wind = rounded(synthetic.wind_fields(nx, ny, nz, 11), dtype)
     phis = rounded(synthetic.scalar_fields(nx, ny, nz, 3, 12), dtype)
     got = run_scalars(pw, m, wind, phis)
@@ -65,10 +68,10 @@ def test_scalars_match_oracle(pw, shape, dtype):
 
 
 @pytest.mark.parametrize("n", [1, 2, 5, 9, 16])
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_scalar_counts_and_groups(pw, n, dtype):
+@pytest.mark.parametrize("dtype,algo", [("f64", "split"), ("f64", "native"), ("f32", "auto")])
+def test_scalar_counts_and_groups(pw, n, dtype, algo):
     nx, ny, nz = 21, 34, 70
-    m = pw.Mesh(nx, ny, nz, 40.0, dtype=dtype)
+    m = pw.Mesh(nx, ny, nz, 40.0, dtype=dtype, algo=algo)
     wind = rounded(synthetic.wind_fields(nx, ny, nz, 13), dtype)
     phis = rounded(synthetic.scalar_fields(nx, ny, nz, n, 14), dtype)
     got = run_scalars(pw, m, wind, phis)
@@ -80,9 +83,10 @@ def test_scalar_counts_and_groups(pw, n, dtype):
 
 
 @pytest.mark.parametrize("tile", [(1, 16), (2, 7), (4, 64), (8, 32), (3, 200)])
-def test_scalar_tiles_do_not_change_results(pw, tile):
+@pytest.mark.parametrize("algo", ["split", "native"])
+def test_scalar_tiles_do_not_change_results(pw, tile, algo):
     nx, ny, nz = 45, 29, 40
-    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64")
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo=algo)
     wind = synthetic.wind_fields(nx, ny, nz, 15)
     phis = synthetic.scalar_fields(nx, ny, nz, 4, 16)
     base = run_scalars(pw, m, wind, phis)
@@ -92,10 +96,10 @@ def test_scalar_tiles_do_not_change_results(pw, tile):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_scalar_accumulate(pw, dtype):
+@pytest.mark.parametrize("dtype,algo", [("f64", "split"), ("f64", "native"), ("f32", "auto")])
+def test_scalar_accumulate(pw, dtype, algo):
     nx, ny, nz = 19, 22, 17
-    m = pw.Mesh(nx, ny, nz, 30.0, dtype=dtype)
+    m = pw.Mesh(nx, ny, nz, 30.0, dtype=dtype, algo=algo)
     wind = rounded(synthetic.wind_fields(nx, ny, nz, 17), dtype)
     phis = rounded(synthetic.scalar_fields(nx, ny, nz, 2, 18), dtype)
     rng = np.random.default_rng(19)
@@ -109,9 +113,10 @@ def test_scalar_accumulate(pw, dtype):
         compare(f"s{q}", got[q], ref + init[q], cond + np.abs(init[q]), 2 * tn, 2 * tc)
 
 
-def test_scalar_uniform_and_lid(pw):
+@pytest.mark.parametrize("algo", ["split", "native"])
+def test_scalar_uniform_and_lid(pw, algo):
     nx, ny, nz = 12, 10, 9
-    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64")
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo=algo)
     U, V, W = np.full((nx, ny, nz), 4.0), np.full((nx, ny, nz), -2.0), np.zeros((nx, ny, nz))
     got = run_scalars(pw, m, (U, V, W), [np.full((nx, ny, nz), 301.5)])
     assert not got[0].any()
@@ -162,13 +167,13 @@ def test_scalar_argument_errors(pw):
     assert m.device_status() == 0
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_scalars_full_size_sampled(pw, dtype):
-    """1024x1024x128 (the bandwidth workload), two scalars, the default launch:
+@pytest.mark.parametrize("dtype,algo", KINDS)
+def test_scalars_full_size_sampled(pw, dtype, algo):
+    """1024x1024x128 (the bandwidth workload), two scalars, the default tiles:
     every sampled output against the oracle evaluated point by point."""
     wl = synthetic.LARGE
     nx, ny, nz = wl.nx, wl.ny, wl.nz
-    m = pw.Mesh(nx, ny, nz, wl.dx, wl.dy, dtype=dtype)
+    m = pw.Mesh(nx, ny, nz, wl.dx, wl.dy, dtype=dtype, algo=algo)
     wind = rounded(synthetic.fields_for(wl), dtype)
     phis = rounded(synthetic.scalar_fields(nx, ny, nz, 2, wl.seed + 100), dtype)
     U = [m.from_interior(a) for a in wind]
@@ -188,3 +193,18 @@ def test_scalars_full_size_sampled(pw, dtype):
         ref, cond = oracle.scalar_points(c, *wind, phi, pts)
         got = m.interior(S[q])[idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
         compare(f"s{q}", got, ref, cond, tn, tc)
+
+
+@pytest.mark.parametrize("scale", [1e-6, 1e3, 1e9])
+def test_split_scalars_magnitude_range(pw, scale):
+    """The double-float path keeps 1e-12 of the condition sum across magnitudes,
+    with mixed signs and exact zeros in the scalar."""
+    nx, ny, nz = 23, 19, 33
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo="split")
+    wind = synthetic.wind_fields(nx, ny, nz, 25)
+    rng = np.random.default_rng(26)
+    phi = scale * rng.standard_normal((nx, ny, nz))
+    phi[rng.random((nx, ny, nz)) < 0.1] = 0.0
+    got = run_scalars(pw, m, wind, [phi])
+    ref, cond = oracle.advect_scalar(oracle.Coeffs(nz, 50.0, 50.0), *wind, phi, want_cond=True)
+    compare("s", got[0], ref, cond, TOL_F64, TOL_F64)
