@@ -272,6 +272,10 @@ def run_gpu(args):
         extras["residuals"] = {"ms_per_call": round(dt * 1e3, 3), "R_E": re, "R_M": rm}
 
     if not args.no_extras and hd == "f64":
+        extras["scalars"] = bench_scalars(args, world, hbm)
+        torch.cuda.empty_cache()
+        extras["paper_strong_f32"] = bench_paper_strong(args, world, hbm)
+        torch.cuda.empty_cache()
         extras["batched"] = bench_batched(args, world, hbm)
         torch.cuda.empty_cache()
         extras["adjoint_loop"] = bench_adjoint_loop(args)
@@ -279,27 +283,31 @@ def run_gpu(args):
         extras["precision"] = bench_precision()
         torch.cuda.empty_cache()
 
-    # ---------------- e2e: pinned host buffers through the public API --------
-    host_in = [torch.empty(m64.shape, dtype=m64.in_dtype, pin_memory=True) for _ in range(3)]
-    host_out = [torch.empty(m64.shape, dtype=m64.out_dtype, pin_memory=True) for _ in range(3)]
-    for h, d in zip(host_in, U64):
-        h.copy_(d)
+    # ---------------- e2e: host arrays through the C-ABI (pw_advect_host) ----
+    # pinned host arrays in, sources back in host arrays; the copies of each
+    # x-slab overlap the halo fill and stencil of its neighbours
+    pipe = api.Pipeline(m64)
+    host_in = [pipe.empty_host() for _ in range(3)]
+    host_out = [pipe.empty_host(out=True) for _ in range(3)]
+    for h, a in zip(host_in, (u, v, w)):
+        h[2:nx + 2, 2:ny + 2, :nz] = torch.from_numpy(a).to(h.dtype)
     stream = torch.cuda.current_stream()
 
     def e2e_step(rec):
-        for h, d in zip(host_in, U64):
-            d.copy_(h, non_blocking=True)
-        m64.halo(*U64, stream=stream)
-        m64.advect(*U64, *S64, stream=stream)
-        for h, d in zip(host_out, S64):
-            h.copy_(d, non_blocking=True)
+        pipe.advect_host(*host_in, *host_out, stream=stream)
 
     e2e_steps = max(3, args.steps // 4)
     e2e_total, _ = time_steps(e2e_step, e2e_steps, 2, world)
-    bytes_in = sum(h.numel() * h.element_size() for h in host_in)
-    bytes_out = sum(h.numel() * h.element_size() for h in host_out)
+    assert m64.device_status() == 0
+    row_in = ny * m64.nzp * host_in[0].element_size()
+    row_out = ny * m64.nzp * host_out[0].element_size()
+    cols_in = nx + (1 if pipe.nslab > 1 else 0)   # column nx-1 travels first, once more
     e2e = {"value": world * pts * e2e_steps / e2e_total, "unit": UNIT,
-           "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out}
+           "h2d_bytes_per_step": 3 * cols_in * row_in, "d2h_bytes_per_step": 3 * nx * row_out,
+           "api": "pw_advect_host (pinned host arrays, x-slabs of %d columns, %d slabs)" % (pipe.slab, pipe.nslab)}
+    err = max(float((host_out[q][2:nx + 2, 2:ny + 2, :nz].to(s64[q].device) - s64[q]).abs().max()) for q in range(3))
+    e2e["max_abs_diff_vs_device_path"] = err
+    del pipe
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -376,6 +384,79 @@ def bench_batched(args, world, hbm):
             "per_member_launch_ms_per_step": round(per_loop * 1e3, 4),
             "speedup_vs_per_member_launches": round(per_loop / per, 3),
             "gpu_launches_per_step": 3}
+
+
+SCALAR_BYTES = {"f64": (8, 8), "f32": (4, 4), "bf16": (2, 4)}
+
+
+def bench_scalars(args, world, hbm):
+    """theta + 5 moisture fields (the paper's tank experiment advects five q
+    fields) on 1024 x 1024 x 128, advected by the same wind in one launch per
+    step; every storage type.  Rate = scalar values produced per second."""
+    import torch
+    from paper_2009_12850_b300 import api
+    wl, n = WL, 6
+    wind = synthetic.fields_for(wl)
+    phis = synthetic.scalar_fields(wl.nx, wl.ny, wl.nz, n, wl.seed + 100)
+    pts = wl.points
+    out = {"workload": f"{wl.name}, theta + 5 q", "scalars": n}
+    for dtype, algo in (("f64", "auto"), ("f64", "native"), ("f32", "auto"), ("bf16", "auto")):
+        m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype, algo=algo)
+        U = [m.from_interior(a) for a in wind]
+        P = [m.from_interior(a) for a in phis]
+        S = [m.empty_out() for _ in range(n)]
+        stream = torch.cuda.current_stream()
+
+        def step(rec):
+            if rec is None:
+                m.advect_scalars(*U, P, S, stream=stream)
+                return
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.advect_scalars(*U, P, S, stream=stream)
+            b.record(stream)
+            rec.append((a, b))
+        steps = max(3, args.steps // 2)
+        tot, kms = time_steps(step, steps, 3, world)
+        assert m.device_status() == 0
+        ei, eo = SCALAR_BYTES[dtype]
+        bpp = 3 * ei + n * (ei + eo)
+        key = dtype if algo == "auto" else "f64_native"
+        out[key] = {"value": world * pts * n * steps / tot, "unit": "scalar values/s",
+                    "kernel_ms": round(kms, 4), "bytes_per_point": bpp,
+                    "hbm_frac": round(bpp * pts / (kms * 1e-3) / 1e9 / hbm, 4)}
+        del m, U, P, S
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_paper_strong(args, world, hbm):
+    """The paper's strong-scaling global domain (2048 x 2048 x 64) held on one
+    GPU in FP32: halo fill + stencil per step."""
+    import torch
+    from paper_2009_12850_b300 import api
+    wl = synthetic.PAPER_STRONG
+    m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype="f32")
+    U = [m.from_interior(a) for a in synthetic.fields_for(wl)]
+    S = [m.empty_out() for _ in range(3)]
+    stream = torch.cuda.current_stream()
+
+    def step(rec):
+        m.halo(*U, stream=stream)
+        if rec is None:
+            m.advect(*U, *S, stream=stream)
+            return
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.advect(*U, *S, stream=stream)
+        b.record(stream)
+        rec.append((a, b))
+    steps = max(3, args.steps // 2)
+    tot, kms = time_steps(step, steps, 3, world)
+    assert m.device_status() == 0
+    pts = wl.points
+    return {"workload": wl.name, "dtype": "f32", "value": world * pts * steps / tot, "unit": UNIT,
+            "kernel_ms": round(kms, 4), "hbm_frac": round(24 * pts / (kms * 1e-3) / 1e9 / hbm, 4)}
 
 
 def bench_adjoint_loop(args):

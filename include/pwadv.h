@@ -201,6 +201,47 @@ pw_status pw_advect(const pw_mesh *mesh, const void *u, const void *v, const voi
 pw_status pw_advect_scalars(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
                             const void *const *phi, void *const *sphi, int beta, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Fields in host memory: the step with its copies overlapped (the hybrid
+ * offload of sections 3 and 3.1, where u, v, w go to the device every timestep
+ * and the sources come back, asynchronously, to be integrated as they arrive).
+ * -------------------------------------------------------------------------*/
+typedef struct pw_pipeline pw_pipeline;
+
+/* Called on a CUDA host thread once columns [i0, i1) of su, sv, sw are in the
+ * host arrays; it must not call CUDA. */
+typedef void (*pw_slab_fn)(void *user, int i0, int i1);
+
+/* A pipeline for one mesh (which must outlive it): device copies of the six
+ * fields (owned), three streams and per-slab events.  slab = x columns per
+ * copy/compute unit (0: nx/16 rounded up).  Synchronises the device once. */
+pw_status pw_pipeline_create(const pw_mesh *mesh, int slab, pw_pipeline **out);
+void pw_pipeline_destroy(pw_pipeline *p);
+/* slab width and number of slabs in use */
+pw_status pw_pipeline_slab(const pw_pipeline *p, int *slab, int *nslab);
+/* block the calling host thread until the last pw_advect_host has finished */
+pw_status pw_pipeline_sync(pw_pipeline *p);
+/* the six device copies u, v, w, su, sv, sw (library layout), e.g. to reuse
+ * them with the device entry points; owned by the pipeline */
+pw_status pw_pipeline_device_fields(const pw_pipeline *p, void **fields6);
+
+/* The halo fill + PW step of pw_halo_periodic + pw_advect on HOST arrays in the
+ * library layout: u, v, w (mesh dtype) in, su, sv, sw (source dtype) out
+ * (beta = 1 adds to them, their old values travelling to the device too).
+ * Only interior rows of the host arrays are read and written; host halos are
+ * neither read nor filled.  Work proceeds in x-slabs: copy-in of slab s,
+ * device halos, the stencil of slab s-1, copy-out of finished slabs, all on the
+ * pipeline's own streams, ordered after the work already queued on `stream`;
+ * `stream` then waits for the whole step, and the call returns without
+ * blocking (except that, when on_slab was given to the previous call, it waits
+ * for that call's callbacks to finish).  on_slab (may be NULL) is called, with
+ * user, after each slab of the sources has reached the host.  Host arrays
+ * should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to
+ * overlap; pageable memory works but serialises them.  Inputs and outputs
+ * must not overlap. */
+pw_status pw_advect_host(pw_pipeline *p, const void *u, const void *v, const void *w, void *su, void *sv,
+                         void *sw, int beta, pw_slab_fn on_slab, void *user, void *stream);
+
 /* Adjoint (transpose of the Jacobian of the map (u,v,w) -> (su,sv,sw) at the
  * given u, v, w) applied to incoming gradients gsu, gsv, gsw, with the periodic
  * halo fold included: gu, gv, gw receive gradients with respect to the INTERIOR

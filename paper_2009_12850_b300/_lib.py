@@ -60,6 +60,12 @@ _SIGS = {
     "pw_halo_fold": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_advect": ([_vp] + [_vp] * 6 + [_i, _vp], _i),
     "pw_advect_scalars": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp], _i),
+    "pw_pipeline_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
+    "pw_pipeline_destroy": ([_vp], None),
+    "pw_pipeline_slab": ([_vp, _ip, _ip], _i),
+    "pw_pipeline_sync": ([_vp], _i),
+    "pw_pipeline_device_fields": ([_vp, ctypes.POINTER(_vp)], _i),
+    "pw_advect_host": ([_vp] + [_vp] * 6 + [_i, _vp, _vp, _vp], _i),
     "pw_advect_adjoint": ([_vp] + [_vp] * 9 + [_d, _i, _vp], _i),
     "pw_euler_adjoint": ([_vp] + [_vp] * 9 + [_d, _vp], _i),
     "pw_euler": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
@@ -168,6 +174,41 @@ def pw_advect_scalars(mesh, u, v, w, phi, sphi, beta, stream):
     """phi, sphi: sequences of device pointers (one per scalar)."""
     check(_c.pw_advect_scalars(mesh, u, v, w, len(phi), _ptrs(phi), _ptrs(sphi), int(beta), stream),
           "pw_advect_scalars")
+
+
+SLAB_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
+
+
+def pw_pipeline_create(mesh, slab):
+    out = _vp()
+    check(_c.pw_pipeline_create(mesh, int(slab), ctypes.byref(out)), "pw_pipeline_create")
+    return out
+
+
+def pw_pipeline_destroy(p):
+    _c.pw_pipeline_destroy(p)
+
+
+def pw_pipeline_slab(p):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(_c.pw_pipeline_slab(p, ctypes.byref(a), ctypes.byref(b)), "pw_pipeline_slab")
+    return a.value, b.value
+
+
+def pw_pipeline_sync(p):
+    check(_c.pw_pipeline_sync(p), "pw_pipeline_sync")
+
+
+def pw_pipeline_device_fields(p):
+    arr = (_vp * 6)()
+    check(_c.pw_pipeline_device_fields(p, arr), "pw_pipeline_device_fields")
+    return [arr[q] for q in range(6)]
+
+
+def pw_advect_host(p, u, v, w, su, sv, sw, beta, on_slab, user, stream):
+    """on_slab: a SLAB_FN instance or None (the caller keeps it alive)."""
+    fn = ctypes.cast(on_slab, _vp) if on_slab is not None else None
+    check(_c.pw_advect_host(p, u, v, w, su, sv, sw, int(beta), fn, user, stream), "pw_advect_host")
 
 
 def pw_advect_adjoint(mesh, u, v, w, gsu, gsv, gsw, gu, gv, gw, alpha, beta, stream):

@@ -241,3 +241,61 @@ class Batch:
 
     def status(self, clear=True, stream=None):
         return L.pw_batch_status(self.handle, clear, _stream(stream))
+
+
+class Pipeline:
+    """The halo fill + PW step on fields in host memory, with the copies
+    overlapped slab by slab (pw_advect_host).  Host tensors are CPU tensors of
+    the mesh shape and dtype, ideally pinned; the pipeline keeps device copies
+    of the six fields."""
+
+    def __init__(self, mesh, slab=0):
+        self.mesh = mesh
+        self.handle = L.pw_pipeline_create(mesh.handle, slab)
+        self.slab, self.nslab = L.pw_pipeline_slab(self.handle)
+        self._cb = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.pw_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _host(self, t, name, out=False):
+        m = self.mesh
+        want = m.out_dtype if out else m.in_dtype
+        if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+            raise TypeError(f"{name} must be a CPU tensor")
+        if t.dtype != want:
+            raise TypeError(f"{name} must be {want}, got {t.dtype}")
+        if t.numel() != m.total or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with {m.total} elements (shape {m.shape})")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def empty_host(self, out=False, pin=True):
+        m = self.mesh
+        return torch.zeros(m.shape, dtype=m.out_dtype if out else m.in_dtype, pin_memory=pin)
+
+    def advect_host(self, u, v, w, su, sv, sw, beta=0, on_slab=None, stream=None):
+        """on_slab(i0, i1) runs on a CUDA host thread as each slab of the
+        sources lands in the host arrays (it must not call CUDA)."""
+        ins = [self._host(t, n) for t, n in ((u, "u"), (v, "v"), (w, "w"))]
+        outs = [self._host(t, n, True) for t, n in ((su, "su"), (sv, "sv"), (sw, "sw"))]
+        cb = None
+        if on_slab is not None:
+            cb = L.SLAB_FN(lambda user, i0, i1: on_slab(i0, i1))
+        L.pw_advect_host(self.handle, *ins, *outs, beta, cb, None, _stream(stream))
+        self._cb = cb  # kept alive until the next call (which waits for these callbacks)
+
+    def sync(self):
+        L.pw_pipeline_sync(self.handle)
+
+    def device_pointers(self):
+        """Device addresses of the pipeline's copies of u, v, w, su, sv, sw
+        (library layout, owned by the pipeline)."""
+        return [p.value if hasattr(p, "value") else p for p in L.pw_pipeline_device_fields(self.handle)]
