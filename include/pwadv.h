@@ -177,6 +177,20 @@ pw_status pw_halo_fold(const pw_mesh *mesh, void *f1, void *f2, void *f3, void *
 pw_status pw_advect(const pw_mesh *mesh, const void *u, const void *v, const void *w,
                     void *su, void *sv, void *sw, int beta, void *stream);
 
+/* The forward Euler step fused into the stencil (the "step fields" integration
+ * of section 3 done on the device, advection-only): with halos of u, v, w
+ * filled,
+ *   un = u + dt su(u,v,w),  vn = v + dt sv(u,v,w),  wn = w + dt sw(u,v,w)
+ * on interior points k < nz, AND on their periodic halo images, so un, vn, wn
+ * are ready for the next step without a halo fill; wn(nz-1) = 0 (the lid).
+ * One pass: the fields are read once and the new state written once (the
+ * separate pw_advect + pw_euler sequence moves 2.5 times the bytes).  un, vn,
+ * wn have the mesh dtype (BF16 results are rounded to bf16).  The sources are
+ * those of pw_advect (same accuracy); the update x + dt s is one FMA in the
+ * compute precision.  No argument may alias another. */
+pw_status pw_advect_step(const pw_mesh *mesh, const void *u, const void *v, const void *w,
+                         void *un, void *vn, void *wn, double dt, void *stream);
+
 /* Most scalars one pw_advect_scalars call advects. */
 #define PW_MAX_SCALARS 16
 

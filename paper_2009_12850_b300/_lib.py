@@ -59,6 +59,7 @@ _SIGS = {
     "pw_halo_periodic": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_halo_fold": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_advect": ([_vp] + [_vp] * 6 + [_i, _vp], _i),
+    "pw_advect_step": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
     "pw_advect_scalars": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp], _i),
     "pw_pipeline_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
     "pw_pipeline_destroy": ([_vp], None),
@@ -168,6 +169,10 @@ def pw_halo_fold(mesh, f1, f2, f3, stream):
 
 def pw_advect(mesh, u, v, w, su, sv, sw, beta, stream):
     check(_c.pw_advect(mesh, u, v, w, su, sv, sw, int(beta), stream), "pw_advect")
+
+
+def pw_advect_step(mesh, u, v, w, un, vn, wn, dt, stream):
+    check(_c.pw_advect_step(mesh, u, v, w, un, vn, wn, float(dt), stream), "pw_advect_step")
 
 
 def pw_advect_scalars(mesh, u, v, w, phi, sphi, beta, stream):

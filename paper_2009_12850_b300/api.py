@@ -128,6 +128,15 @@ class Mesh:
                     beta, _stream(stream))
         return su, sv, sw
 
+    def step(self, u, v, w, un=None, vn=None, wn=None, dt=1.0, stream=None):
+        """Fused forward Euler step: (un, vn, wn) = x + dt S(x), halos included."""
+        un = self.empty() if un is None else un
+        vn = self.empty() if vn is None else vn
+        wn = self.empty() if wn is None else wn
+        L.pw_advect_step(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                         self._check(un, "un"), self._check(vn, "vn"), self._check(wn, "wn"), dt, _stream(stream))
+        return un, vn, wn
+
     def advect_scalars(self, u, v, w, phis, sources=None, beta=0, stream=None):
         """PW sources of the cell-centred scalars phis (list of field tensors
         with halos filled) advected by (u, v, w); returns the list of sources."""

@@ -20,6 +20,19 @@ pw_advect_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
                                                blockIdx.z * g.kc);
 }
 
+// the forward Euler step fused into the stencil: xn = x + dt S(x), halos included
+template <typename TS, typename TC, int KV>
+__global__ void __launch_bounds__(512)
+pw_step_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
+              const __grid_constant__ CUtensorMap mw, TS *__restrict__ un, TS *__restrict__ vn,
+              TS *__restrict__ wn, const TC *__restrict__ coef, const PwGeom g, double dt,
+              int *__restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    if (pw_status_failed(status)) return;
+    pw_march_tile<TS, TC, TS, KV, PW_MARCH_NS, true>(&mu, &mv, &mw, un, vn, wn, coef, g, 0, status, smem_raw,
+                                                     blockIdx.x * g.tj, blockIdx.y * g.ti, blockIdx.z * g.kc, dt);
+}
+
 // --------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------
@@ -33,10 +46,10 @@ static int pw_lcm(int a, int b) {
     return a / x * b;
 }
 
-template <typename TS, typename TC, typename TO, int KV>
+template <typename TS, typename TC, typename TO, int KV, bool STEP = false>
 static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v, const void *w,
                                  void *su, void *sv, void *sw, int beta, cudaStream_t st,
-                                 int tile_j, int tile_i, int ns) {
+                                 int tile_j, int tile_i, int ns, double dt = 0.0) {
     PwGeom g;
     g.nx = m->nx;
     g.ny = m->ny;
@@ -70,7 +83,10 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
                                         g.kb, tile_j + 2);
         if (s != PW_OK) return s;
     }
-    auto kern = pw_advect_march<TS, TC, TO, KV>;
+    const auto kern = [] {
+        if constexpr (STEP) return pw_step_march<TS, TC, KV>;
+        else return pw_advect_march<TS, TC, TO, KV>;
+    }();
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)((m->nz + g.kc - 1) / g.kc));
@@ -78,8 +94,12 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
     const TC *coef = std::is_same<TC, double>::value
                          ? reinterpret_cast<const TC *>(m->coef64 + 6 * m->nz)
                          : reinterpret_cast<const TC *>(m->coef32);
-    kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (TO *)su, (TO *)sv, (TO *)sw, coef,
-                                      g, beta, m->status);
+    if constexpr (STEP)
+        kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (TS *)su, (TS *)sv, (TS *)sw, coef, g, dt,
+                                          m->status);
+    else
+        kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (TO *)su, (TO *)sv, (TO *)sw, coef,
+                                          g, beta, m->status);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
 }
@@ -106,6 +126,27 @@ pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const
     return pw_fail(PW_ERR_DTYPE, "unknown dtype");
 }
 
+pw_status pw_launch_step_split(const pw_mesh *m, const void *u, const void *v, const void *w, void *un,
+                               void *vn, void *wn, double dt, cudaStream_t st, int tile_j, int tile_i);
+
+pw_status pw_launch_step(const pw_mesh *m, const void *u, const void *v, const void *w, void *un, void *vn,
+                         void *wn, double dt, cudaStream_t st, int tile_j, int tile_i) {
+    switch (m->dtype) {
+        case PW_F64:
+            if (m->algo == PW_ALGO_F64_SPLIT)
+                return pw_launch_step_split(m, u, v, w, un, vn, wn, dt, st, tile_j, tile_i);
+            return pw_launch_march<double, double, double, 2, true>(m, u, v, w, un, vn, wn, 0, st, tile_j, tile_i,
+                                                                    PW_MARCH_NS, dt);
+        case PW_F32:
+            return pw_launch_march<float, float, float, 4, true>(m, u, v, w, un, vn, wn, 0, st, tile_j, tile_i,
+                                                                 PW_MARCH_NS, dt);
+        case PW_BF16:
+            return pw_launch_march<__nv_bfloat16, float, __nv_bfloat16, 4, true>(m, u, v, w, un, vn, wn, 0, st,
+                                                                                 tile_j, tile_i, PW_MARCH_NS, dt);
+    }
+    return pw_fail(PW_ERR_DTYPE, "unknown dtype");
+}
+
 static pw_status pw_check_fields(const void *const *p, const char *const *nm, int n) {
     for (int q = 0; q < n; q++) {
         pw_status s = pw_check_ptr(p[q], nm[q]);
@@ -127,4 +168,18 @@ extern "C" pw_status pw_advect(const pw_mesh *m, const void *u, const void *v, c
             if (p[a] == p[b]) return pw_fail(PW_ERR_ARG, "%s and %s alias", nm[a], nm[b]);
     if (su == sv || su == sw || sv == sw) return pw_fail(PW_ERR_ARG, "outputs alias");
     return pw_launch_advect(m, u, v, w, su, sv, sw, beta, (cudaStream_t)stream, m->tile_j, m->tile_i);
+}
+
+extern "C" pw_status pw_advect_step(const pw_mesh *m, const void *u, const void *v, const void *w, void *un,
+                                    void *vn, void *wn, double dt, void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    const void *p[6] = {u, v, w, un, vn, wn};
+    const char *nm[6] = {"u", "v", "w", "un", "vn", "wn"};
+    pw_status s = pw_check_fields(p, nm, 6);
+    if (s != PW_OK) return s;
+    for (int a = 0; a < 6; a++)
+        for (int b = a + 1; b < 6; b++)
+            if (p[a] == p[b]) return pw_fail(PW_ERR_ARG, "%s and %s alias", nm[a], nm[b]);
+    if (!(dt == dt) || dt - dt != 0.0) return pw_fail(PW_ERR_ARG, "dt must be finite");
+    return pw_launch_step(m, u, v, w, un, vn, wn, dt, (cudaStream_t)stream, m->tile_j, m->tile_i);
 }

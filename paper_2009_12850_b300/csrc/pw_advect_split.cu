@@ -24,6 +24,7 @@
 
 #include "pw_df.cuh"
 #include "pw_internal.h"
+#include "pw_march.cuh"  // pw_store_images
 
 struct PwSplitGeom {
     int nx, ny, nz, kc, kb, tj, ti;
@@ -35,13 +36,17 @@ struct PwSplitGeom {
     long long si, sj;
 };
 
-template <int NS, int TJ, bool BETA>
+// STEP: write x + dt S(x) (x read exactly from xu, xv, xw) to su, sv, sw and to
+// their periodic halo images, the forward Euler step fused into the stencil
+template <int NS, int TJ, bool BETA, bool STEP = false>
 __global__ void __launch_bounds__(256, 2)
 pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                        const __grid_constant__ CUtensorMap mw, double *__restrict__ su,
                        double *__restrict__ sv, double *__restrict__ sw,
                        const float *__restrict__ cs, const PwSplitGeom g,
-                       int *__restrict__ status) {
+                       int *__restrict__ status, const double *__restrict__ xu = nullptr,
+                       const double *__restrict__ xv = nullptr, const double *__restrict__ xw = nullptr,
+                       double dt = 0.0) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double *planes = reinterpret_cast<double *>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * 3 * g.field_stride * 8);
@@ -234,7 +239,22 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
         double c0 = join(lx(rw.h), lx(rw.l)), c1 = join(ly(rw.h), ly(rw.l));
         if (kbase >= g.nz - 1) c0 = 0.0;
         if (kbase + 1 >= g.nz - 1) c1 = 0.0;
-        if (kbase + 1 < g.nz) {
+        if constexpr (STEP) {
+            // x exactly from memory (the staged planes now hold (hi, lo) pairs);
+            // the lid level of w is not a degree of freedom and stays 0
+            const bool two = kbase + 1 < g.nz;
+            double xu0 = xu[off], xv0 = xv[off], xw0 = xw[off];
+            double xu1 = two ? xu[off + 1] : 0.0, xv1 = two ? xv[off + 1] : 0.0, xw1 = two ? xw[off + 1] : 0.0;
+            if (kbase >= g.nz - 1) xw0 = 0.0;
+            if (kbase + 1 >= g.nz - 1) xw1 = 0.0;
+            const double ru2[2] = {fma(dt, a0, xu0), fma(dt, a1, xu1)};
+            const double rv2[2] = {fma(dt, b0, xv0), fma(dt, b1, xv1)};
+            const double rw2[2] = {fma(dt, c0, xw0), fma(dt, c1, xw1)};
+            const int nvalid = g.nz - kbase;
+            pw_store_images<double, 2>(su, i, j, kbase, ru2, nvalid, g.nx, g.ny, g.si, g.sj);
+            pw_store_images<double, 2>(sv, i, j, kbase, rv2, nvalid, g.nx, g.ny, g.si, g.sj);
+            pw_store_images<double, 2>(sw, i, j, kbase, rw2, nvalid, g.nx, g.ny, g.si, g.sj);
+        } else if (kbase + 1 < g.nz) {
             double2 *pu = reinterpret_cast<double2 *>(su + off);
             double2 *pv = reinterpret_cast<double2 *>(sv + off);
             double2 *pw = reinterpret_cast<double2 *>(sw + off);
@@ -253,9 +273,9 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     }
 }
 
-pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v, const void *w,
+static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v, const void *w,
                                  void *su, void *sv, void *sw, int beta, cudaStream_t st,
-                                 int tile_j, int tile_i) {
+                                 int tile_j, int tile_i, bool step, double dt) {
     constexpr int NS = 5;
     // compiled for 4 or 8 rows of columns per CTA (the nearest of the two is used)
     tile_j = tile_j <= 5 ? 4 : 8;
@@ -291,14 +311,28 @@ pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v,
                                         tile_j + 2);
         if (s != PW_OK) return s;
     }
-    auto kern = tile_j == 4 ? (beta ? pw_advect_split_kernel<NS, 4, true> : pw_advect_split_kernel<NS, 4, false>)
-                            : (beta ? pw_advect_split_kernel<NS, 8, true> : pw_advect_split_kernel<NS, 8, false>);
+    auto kern = step ? (tile_j == 4 ? pw_advect_split_kernel<NS, 4, false, true>
+                                    : pw_advect_split_kernel<NS, 8, false, true>)
+                     : tile_j == 4 ? (beta ? pw_advect_split_kernel<NS, 4, true> : pw_advect_split_kernel<NS, 4, false>)
+                                   : (beta ? pw_advect_split_kernel<NS, 8, true> : pw_advect_split_kernel<NS, 8, false>);
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)((m->nz + g.kc - 1) / g.kc));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");
     kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (double *)su, (double *)sv, (double *)sw,
-                                      m->coefsplit, g, m->status);
+                                      m->coefsplit, g, m->status, (const double *)u, (const double *)v,
+                                      (const double *)w, dt);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
+}
+
+pw_status pw_launch_advect_split(const pw_mesh *m, const void *u, const void *v, const void *w,
+                                 void *su, void *sv, void *sw, int beta, cudaStream_t st,
+                                 int tile_j, int tile_i) {
+    return pw_launch_split(m, u, v, w, su, sv, sw, beta, st, tile_j, tile_i, false, 0.0);
+}
+
+pw_status pw_launch_step_split(const pw_mesh *m, const void *u, const void *v, const void *w, void *un,
+                               void *vn, void *wn, double dt, cudaStream_t st, int tile_j, int tile_i) {
+    return pw_launch_split(m, u, v, w, un, vn, wn, 0, st, tile_j, tile_i, true, dt);
 }

@@ -64,6 +64,8 @@ static inline int pw_kdim(int nz, int field) { return field == 2 ? (nz > 1 ? nz 
 pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const void *w,
                            void *su, void *sv, void *sw, int beta, cudaStream_t st,
                            int tile_j, int tile_i);
+pw_status pw_launch_step(const pw_mesh *m, const void *u, const void *v, const void *w, void *un, void *vn,
+                         void *wn, double dt, cudaStream_t st, int tile_j, int tile_i);
 pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
                                    const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
                                    int tile_j, int tile_i, int group);

@@ -147,6 +147,22 @@ __device__ __forceinline__ void pw_copy(TC (&d)[KV + 2], const TC (&s)[KV + 2]) 
 }
 
 // --------------------------------------------------------------------------
+// store KV values of interior column (i, j) at the column and at every halo
+// column that is its periodic image (halo coordinates ih, jh in [0, n+4))
+// --------------------------------------------------------------------------
+template <typename TO, int KV>
+__device__ __forceinline__ void pw_store_images(TO *base, int i, int j, int kbase, const TO (&r)[KV],
+                                                int nvalid, int nx, int ny, long long si, long long sj) {
+    pw_store<TO, KV>(base + (long long)(i + 2) * si + (long long)(j + 2) * sj + kbase, r, nvalid, 0);
+    if (i >= 2 && i < nx - 2 && j >= 2 && j < ny - 2) return;
+    for (int ih = i + 2 - ((i + 2) / nx) * nx; ih < nx + 4; ih += nx)
+        for (int jh = j + 2 - ((j + 2) / ny) * ny; jh < ny + 4; jh += ny) {
+            if (ih >= 2 && ih < nx + 2 && jh >= 2 && jh < ny + 2) continue;  // the interior column
+            pw_store<TO, KV>(base + (long long)ih * si + (long long)jh * sj + kbase, r, nvalid, 0);
+        }
+}
+
+// --------------------------------------------------------------------------
 // one tile of the x-march: tile_j rows from j0, columns i0 .. i0+tile_i-1, the
 // k chunk starting at k0.  Shared memory: NS plane slots then NS mbarriers
 // (initialised here, invalidated before returning so the caller may run the
@@ -159,13 +175,18 @@ __device__ __forceinline__ void pw_copy(TC (&d)[KV + 2], const TC (&s)[KV + 2]) 
 // at or above nz (and the w lid) arrive from TMA as zeros: the tensor maps
 // carry the logical k extent.
 // --------------------------------------------------------------------------
-template <typename TS, typename TC, typename TO, int KV, int NS>
+//
+// STEP: instead of the sources, write x + dt S(x) for x = u, v, w (the forward
+// Euler step fused into the stencil: x is the centre value already in
+// registers) to su, sv, sw, which then have the field type, at the interior
+// column and at its periodic halo images (ready for the next step).
+template <typename TS, typename TC, typename TO, int KV, int NS, bool STEP = false>
 __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUtensorMap *mv_,
                                               const CUtensorMap *mw_, TO *__restrict__ su,
                                               TO *__restrict__ sv, TO *__restrict__ sw,
                                               const TC *__restrict__ coef, const PwGeom &g, int beta,
                                               int *__restrict__ status, unsigned char *smem_raw,
-                                              int j0, int i0, int k0) {
+                                              int j0, int i0, int k0, double dt = 0.0) {
     const CUtensorMap &mu = *mu_, &mv = *mv_, &mw = *mw_;
     TS *planes = reinterpret_cast<TS *>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NS * 3 * g.field_stride * sizeof(TS));
@@ -235,6 +256,7 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
         d2[m] = in ? coef[3 * g.nz + k] : TC(0);
     }
     const TC tcx = (TC)g.tcx, tcy = (TC)g.tcy;
+    const TC tdt = (TC)dt;
     const int L = g.kb;
     const int rS = tjc * L, rC = (tjc + 1) * L, rN = (tjc + 2) * L;
 
@@ -297,22 +319,29 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
                 s = s + tcy * (uS[a] * (vS[a] + vSP[a]) - uN[a] * (vC[a] + vP[a]));
                 s = s + c1[m] * uC[a - 1] * (wC[a - 1] + wP[a - 1]);
                 s = s - c2[m] * uC[a + 1] * (wC[a] + wP[a]);
-                ru[m] = (TO)s;
+                ru[m] = STEP ? (TO)(uC[a] + tdt * s) : (TO)s;
                 s = tcx * (vM[a] * (uM[a] + uNM[a]) - vP[a] * (uC[a] + uN[a]));
                 s = s + tcy * (vS[a] * (vS[a] + vC[a]) - vN[a] * (vC[a] + vN[a]));
                 s = s + c1[m] * vC[a - 1] * (wC[a - 1] + wN[a - 1]);
                 s = s - c2[m] * vC[a + 1] * (wC[a] + wN[a]);
-                rv[m] = (TO)s;
+                rv[m] = STEP ? (TO)(vC[a] + tdt * s) : (TO)s;
                 s = tcx * (wM[a] * (uM[a] + uM[a + 1]) - wP[a] * (uC[a] + uC[a + 1]));
                 s = s + tcy * (wS[a] * (vS[a] + vS[a + 1]) - wN[a] * (vC[a] + vC[a + 1]));
                 s = s + d1[m] * wC[a - 1] * (wC[a - 1] + wC[a]);
                 s = s - d2[m] * wC[a + 1] * (wC[a] + wC[a + 1]);
-                rw[m] = (kbase + m < g.nz - 1) ? (TO)s : TO(0);
+                // the lid level of w reads as 0, so a step leaves it 0
+                rw[m] = (kbase + m < g.nz - 1) ? (STEP ? (TO)(wC[a] + tdt * s) : (TO)s) : TO(0);
             }
-            const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
-            pw_store<TO, KV>(su + off, ru, nvalid, beta);
-            pw_store<TO, KV>(sv + off, rv, nvalid, beta);
-            pw_store<TO, KV>(sw + off, rw, nvalid, beta);
+            if (STEP) {
+                pw_store_images<TO, KV>(su, i, j, kbase, ru, nvalid, g.nx, g.ny, g.si, g.sj);
+                pw_store_images<TO, KV>(sv, i, j, kbase, rv, nvalid, g.nx, g.ny, g.si, g.sj);
+                pw_store_images<TO, KV>(sw, i, j, kbase, rw, nvalid, g.nx, g.ny, g.si, g.sj);
+            } else {
+                const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
+                pw_store<TO, KV>(su + off, ru, nvalid, beta);
+                pw_store<TO, KV>(sv + off, rv, nvalid, beta);
+                pw_store<TO, KV>(sw + off, rw, nvalid, beta);
+            }
         }
         // slide the window one column along x
         pw_copy<TC, KV>(uM, uC);
