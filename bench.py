@@ -276,6 +276,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         extras["paper_strong_f32"] = bench_paper_strong(args, world, hbm)
         torch.cuda.empty_cache()
+        extras["fused_step"] = bench_fused_step(args, world, hbm)
+        torch.cuda.empty_cache()
         extras["batched"] = bench_batched(args, world, hbm)
         torch.cuda.empty_cache()
         extras["adjoint_loop"] = bench_adjoint_loop(args)
@@ -426,6 +428,44 @@ def bench_scalars(args, world, hbm):
                     "kernel_ms": round(kms, 4), "bytes_per_point": bpp,
                     "hbm_frac": round(bpp * pts / (kms * 1e-3) / 1e9 / hbm, 4)}
         del m, U, P, S
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_fused_step(args, world, hbm):
+    """One forward Euler timestep of the wind on 1024 x 1024 x 128: the fused
+    stencil + update (pw_advect_step, halos of the new state written in the same
+    pass) against halo fill + pw_advect + pw_euler."""
+    import torch
+    from paper_2009_12850_b300 import api
+    out = {"workload": WL.name, "dt": 0.5}
+    f = synthetic.fields_for(WL)
+    pts = WL.points
+    for dtype in ("f64", "f32"):
+        m = api.Mesh(WL.nx, WL.ny, WL.nz, WL.dx, WL.dy, dtype=dtype)
+        A = [m.from_interior(a) for a in f]
+        B = [m.empty() for _ in range(3)]
+        cur = [A, B]
+
+        def fused(rec):
+            m.step(*cur[0], *cur[1], dt=0.5)
+            cur.reverse()
+        steps = max(3, args.steps // 2)
+        tf, _ = time_steps(fused, steps, 3, world)
+        S = [m.empty_out() for _ in range(3)]
+
+        def unfused(rec):
+            m.halo(*A)
+            m.advect(*A, *S)
+            m.euler(*A, *S, 0.5)
+        tu, _ = time_steps(unfused, steps, 3, world)
+        assert m.device_status() == 0
+        es = {"f64": 8, "f32": 4}[dtype]
+        out[dtype] = {"fused_value": world * pts * steps / tf, "unfused_value": world * pts * steps / tu,
+                      "unit": UNIT, "fused_ms": round(tf / steps * 1e3, 4), "unfused_ms": round(tu / steps * 1e3, 4),
+                      "speedup": round(tu / tf, 3), "fused_bytes_per_point": 6 * es,
+                      "unfused_bytes_per_point": 15 * es}
+        del m, A, B, S, cur
         torch.cuda.empty_cache()
     return out
 

@@ -228,7 +228,7 @@ typedef void (*pw_slab_fn)(void *user, int i0, int i1);
 
 /* A pipeline for one mesh (which must outlive it): device copies of the six
  * fields (owned), three streams and per-slab events.  slab = x columns per
- * copy/compute unit (0: nx/16 rounded up).  Synchronises the device once. */
+ * copy/compute unit (0: nx/32 rounded up).  Synchronises the device once. */
 pw_status pw_pipeline_create(const pw_mesh *mesh, int slab, pw_pipeline **out);
 void pw_pipeline_destroy(pw_pipeline *p);
 /* slab width and number of slabs in use */

@@ -3,7 +3,8 @@
 ``PWAdvect`` maps (u, v, w) to (su, sv, sw); its backward is the adjoint kernel
 (pw_advect_adjoint).  ``PWEulerSegment`` runs n forward-Euler steps
 x <- x + dt S(x) (advection only; the "step fields" integration of the paper's
-dynamics group, section 3) and keeps only its input: the backward recomputes
+dynamics group, section 3) with the fused step kernel (pw_advect_step) and keeps
+only its input: the backward recomputes
 the segment's states and sweeps them in reverse with the Euler adjoint kernel
 (g <- g + dt J(x)^T g), so a long loop split into segments stores one state
 per segment (checkpointed recomputation).
@@ -47,11 +48,15 @@ class PWAdvect(torch.autograd.Function):
 class PWEulerSegment(torch.autograd.Function):
     @staticmethod
     def forward(ctx, mesh: Mesh, dt: float, nsteps: int, u, v, w):
-        x = [t.clone() for t in (u, v, w)]
-        S = [mesh.empty_out() for _ in range(3)]
-        for _ in range(nsteps):
-            mesh.advect(*x, *S)
-            mesh.euler(*x, *S, dt)
+        # fused steps (stencil + update + halos in one pass), ping-ponged
+        x = [u, v, w]
+        bufs = [[mesh.empty() for _ in range(3)] for _ in range(min(nsteps, 2))]
+        for n in range(nsteps):
+            y = bufs[n % 2]
+            mesh.step(*x, *y, dt=dt)
+            x = y
+        if nsteps == 0:
+            x = [t.clone() for t in x]
         ctx.mesh, ctx.dt, ctx.nsteps = mesh, float(dt), int(nsteps)
         ctx.save_for_backward(u, v, w)
         return tuple(x)
@@ -60,13 +65,9 @@ class PWEulerSegment(torch.autograd.Function):
     def backward(ctx, gu, gv, gw):
         mesh, dt, n = ctx.mesh, ctx.dt, ctx.nsteps
         u, v, w = ctx.saved_tensors
-        states = [[t.clone() for t in (u, v, w)]]
-        S = [mesh.empty_out() for _ in range(3)]
+        states = [[u, v, w]]
         for _ in range(n - 1):
-            x = [t.clone() for t in states[-1]]
-            mesh.advect(*x, *S)
-            mesh.euler(*x, *S, dt)
-            states.append(x)
+            states.append(list(mesh.step(*states[-1], dt=dt)))
         g = [_grad_in(mesh, t, u) for t in (gu, gv, gw)]
         for t in reversed(range(n)):
             g = list(mesh.euler_adjoint(*states[t], *g, dt=dt))

@@ -144,7 +144,7 @@ extern "C" pw_status pw_pipeline_create(const pw_mesh *m, int slab, pw_pipeline 
     if (!m || !out) return pw_fail(PW_ERR_ARG, "mesh and out must not be NULL");
     *out = nullptr;
     if (slab < 0) return pw_fail(PW_ERR_ARG, "slab = %d columns (>= 0)", slab);
-    if (slab == 0) slab = std::max(1, (m->nx + 15) / 16);
+    if (slab == 0) slab = std::max(1, (m->nx + 31) / 32);
     slab = std::min(slab, m->nx);
     pw_pipeline *p = new (std::nothrow) pw_pipeline();
     if (!p) return pw_fail(PW_ERR_NOMEM, "pipeline object");
