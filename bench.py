@@ -238,11 +238,18 @@ def run_gpu(args):
     s64 = [m64.interior(s) for s in S64]
 
     extras = {}
+    rows = None if args.extras is None else set(args.extras.split(","))
+
+    def want(name):
+        return not args.no_extras and hd == "f64" and (rows is None or name in rows)
+
     if not args.no_extras and hd == "f64":
         for dtype, algo_name in (("f32", "auto"), ("bf16", "auto"), ("f64", "native")):
+            key = dtype if algo_name == "auto" else "f64_native"
+            if not want(key):
+                continue
             m, U, S = build(dtype, algo_name)
             tot, kms = time_steps(make_step(m, U, S), max(3, args.steps // 2), 3, world)
-            key = dtype if algo_name == "auto" else "f64_native"
             bpp = BYTES_PER_POINT[dtype]
             err = {}
             for q, nm in enumerate(("su", "sv", "sw")):
@@ -260,6 +267,7 @@ def run_gpu(args):
                 extras[key]["dp_ops_per_point_est"] = 42
             del m, U, S
             torch.cuda.empty_cache()
+    if want("residuals"):
         # conservation reductions (A5) on the FP64 fields
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -271,19 +279,15 @@ def run_gpu(args):
         rm = [float(sums[q, 2] / sums[q, 3]) for q in range(3)]
         extras["residuals"] = {"ms_per_call": round(dt * 1e3, 3), "R_E": re, "R_M": rm}
 
-    if not args.no_extras and hd == "f64":
-        extras["scalars"] = bench_scalars(args, world, hbm)
-        torch.cuda.empty_cache()
-        extras["paper_strong_f32"] = bench_paper_strong(args, world, hbm)
-        torch.cuda.empty_cache()
-        extras["fused_step"] = bench_fused_step(args, world, hbm)
-        torch.cuda.empty_cache()
-        extras["batched"] = bench_batched(args, world, hbm)
-        torch.cuda.empty_cache()
-        extras["adjoint_loop"] = bench_adjoint_loop(args)
-        torch.cuda.empty_cache()
-        extras["precision"] = bench_precision()
-        torch.cuda.empty_cache()
+    for name, fn in (("scalars", lambda: bench_scalars(args, world, hbm)),
+                     ("paper_strong_f32", lambda: bench_paper_strong(args, world, hbm)),
+                     ("fused_step", lambda: bench_fused_step(args, world, hbm)),
+                     ("batched", lambda: bench_batched(args, world, hbm)),
+                     ("adjoint_loop", lambda: bench_adjoint_loop(args)),
+                     ("precision", bench_precision)):
+        if want(name):
+            extras[name] = fn()
+            torch.cuda.empty_cache()
 
     # ---------------- e2e: host arrays through the C-ABI (pw_advect_host) ----
     # pinned host arrays in, sources back in host arrays; the copies of each
@@ -632,6 +636,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="only the headline and e2e")
+    ap.add_argument("--extras", default=None,
+                    help="comma list of extra rows to run (default all): f32, bf16, f64_native, residuals, scalars, "
+                         "paper_strong_f32, fused_step, batched, adjoint_loop, precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64", help="headline storage type")

@@ -369,6 +369,12 @@ pw_status pw_advect_batched(pw_batch *batch, int beta, void *stream);
  * `stream`.  On failure the previous configuration stays in force. */
 pw_status pw_batch_set_tile(pw_batch *batch, int threads, int tile_i, void *stream);
 
+/* Tile schedule of pw_advect_batched: persistent = 1 (default) launches
+ * SMs x occupancy CTAs that pull tiles from a device counter; persistent = 0
+ * launches one CTA per tile (the hardware scheduler hands them out in the same
+ * longest-first order).  pw_batch_autotune tries both. */
+pw_status pw_batch_set_schedule(pw_batch *batch, int persistent, void *stream);
+
 /* Periodic halo fill of the bound u, v, w of every member in one launch. */
 pw_status pw_batch_halo(pw_batch *batch, void *stream);
 

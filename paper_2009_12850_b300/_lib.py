@@ -80,6 +80,7 @@ _SIGS = {
     "pw_batch_halo": ([_vp, _vp], _i),
     "pw_batch_status": ([_vp, _i, _vp, _ip], _i),
     "pw_batch_set_tile": ([_vp, _i, _i, _vp], _i),
+    "pw_batch_set_schedule": ([_vp, _i, _vp], _i),
     "pw_autotune": ([_vp] + [_vp] * 6 + [ctypes.c_char_p, _vp, _fp], _i),
     "pw_batch_autotune": ([_vp, ctypes.c_char_p, _vp, _fp], _i),
     "pw_status_string": ([_i], ctypes.c_char_p),
@@ -282,6 +283,10 @@ def pw_batch_halo(batch, stream):
 
 def pw_batch_set_tile(batch, threads, tile_i, stream):
     check(_c.pw_batch_set_tile(batch, int(threads), int(tile_i), stream), "pw_batch_set_tile")
+
+
+def pw_batch_set_schedule(batch, persistent, stream):
+    check(_c.pw_batch_set_schedule(batch, int(persistent), stream), "pw_batch_set_schedule")
 
 
 def pw_batch_status(batch, clear, stream):

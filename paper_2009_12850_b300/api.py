@@ -248,6 +248,9 @@ class Batch:
     def set_tile(self, threads, tile_i, stream=None):
         L.pw_batch_set_tile(self.handle, threads, tile_i, _stream(stream))
 
+    def set_schedule(self, persistent, stream=None):
+        L.pw_batch_set_schedule(self.handle, persistent, _stream(stream))
+
     def status(self, clear=True, stream=None):
         return L.pw_batch_status(self.handle, clear, _stream(stream))
 

@@ -42,6 +42,7 @@ struct pw_batch_impl {
     std::vector<void *> ptr[6];        // bound u v w su sv sw (by member index)
     bool bound = false;
     int threads = 256, tile_i = 32;
+    int persistent = 1;                // 1: SMs x occupancy CTAs pull tiles; 0: one CTA per tile
     int grid = 0, total_tiles = 0, halo_cols = 0;
     size_t smem = 0;
 };
@@ -52,16 +53,25 @@ struct pw_batch {
 
 static constexpr int PW_BATCH_NS = PW_MARCH_NS;
 
+// persistent = 1: CTAs pull tile numbers from the counter until none is left;
+// persistent = 0: CTA b runs tile b (the hardware block scheduler hands out the
+// tiles in the same longest-first order)
 __global__ void __launch_bounds__(512)
 pw_batch_kernel(const PwBatchMember *__restrict__ members, int n, int total_tiles,
-                int *__restrict__ counter, int *__restrict__ status, int beta) {
+                int *__restrict__ counter, int *__restrict__ status, int beta, int persistent) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_tile;
-    while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
-        __syncthreads();
-        const int t = s_tile;
-        __syncthreads();
+    for (int pass = 0;; pass++) {
+        int t;
+        if (persistent) {
+            if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+            __syncthreads();
+            t = s_tile;
+            __syncthreads();
+        } else {
+            if (pass > 0) return;
+            t = blockIdx.x;
+        }
         if (t >= total_tiles || pw_status_failed(status)) return;
         int lo = 0, hi = n - 1;
         while (lo < hi) {
@@ -206,7 +216,7 @@ static pw_status pw_batch_build(pw_batch_impl &b, cudaStream_t st) {
     int per_sm = 0;
     PW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pw_batch_kernel, b.threads, smem));
     if (per_sm < 1) return pw_fail(PW_ERR_SHAPE, "batch kernel cannot be resident with %d threads", b.threads);
-    b.grid = std::min(b.total_tiles, per_sm * b.meshes[0]->num_sms);
+    b.grid = b.persistent ? std::min(b.total_tiles, per_sm * b.meshes[0]->num_sms) : b.total_tiles;
     PW_CUDA(cudaMemcpyAsync(b.dev, b.host.data(), sizeof(PwBatchMember) * n, cudaMemcpyHostToDevice, st));
     if (b.bound) {
         // the halo launch addresses members by slot: its field table must follow
@@ -304,9 +314,24 @@ extern "C" pw_status pw_batch_set_tile(pw_batch *bb, int threads, int tile_i, vo
     return s;
 }
 
+extern "C" pw_status pw_batch_set_schedule(pw_batch *bb, int persistent, void *stream) {
+    if (!bb) return pw_fail(PW_ERR_ARG, "batch is NULL");
+    if (persistent != 0 && persistent != 1) return pw_fail(PW_ERR_ARG, "persistent must be 0 or 1");
+    pw_batch_impl &b = bb->impl;
+    const int old = b.persistent;
+    b.persistent = persistent;
+    pw_status s = pw_batch_build(b, (cudaStream_t)stream);
+    if (s != PW_OK) {
+        b.persistent = old;
+        pw_batch_build(b, (cudaStream_t)stream);
+    }
+    return s;
+}
+
 static pw_status pw_batch_launch(pw_batch_impl &b, int beta, cudaStream_t st) {
     PW_CUDA(cudaMemsetAsync(b.counter, 0, sizeof(int), st));
-    pw_batch_kernel<<<b.grid, b.threads, b.smem, st>>>(b.dev, b.n, b.total_tiles, b.counter, b.status, beta);
+    pw_batch_kernel<<<b.grid, b.threads, b.smem, st>>>(b.dev, b.n, b.total_tiles, b.counter, b.status, beta,
+                                                       b.persistent);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
 }
@@ -459,35 +484,46 @@ extern "C" pw_status pw_batch_autotune(pw_batch *bb, const char *cache_path, voi
     }
     char key[256];
     snprintf(key, sizeof(key), "batch n=%d shapes=%016llx sms=%d", b.n, hsh, b.meshes[0]->num_sms);
+    // cached: threads, tile_i, and the schedule encoded in the sign of tile_i
+    // (negative: one CTA per tile)
     int th = 0, ti = 0;
     if (pw_cache_lookup(cache_path, key, &th, &ti)) {
         b.threads = th;
-        b.tile_i = ti;
+        b.tile_i = ti < 0 ? -ti : ti;
+        b.persistent = ti < 0 ? 0 : 1;
         if (best_ms) *best_ms = -1.0f;
         return pw_batch_build(b, st);
     }
+    // every CTA size that is a whole number of warps (it sets how many rows of
+    // each member's columns a tile holds, so how many lanes idle), three march
+    // lengths, both schedules
     float best = 1e30f;
-    int bt = b.threads, bi = b.tile_i;
-    for (int t : {64, 128, 256, 384})
-        for (int c : {16, 32, 64, 128}) {
-            b.threads = t;
-            b.tile_i = c;
-            pw_status s = pw_batch_build(b, st);
-            if (s == PW_ERR_SHAPE) continue;
-            if (s != PW_OK) return s;
-            float ms = 0;
-            s = pw_time([&] { return pw_batch_launch(b, 0, st); }, st, &ms);
-            if (s != PW_OK) return s;
-            if (ms < best) {
-                best = ms;
-                bt = t;
-                bi = c;
+    int bt = b.threads, bi = b.tile_i, bp = b.persistent;
+    for (int p : {1, 0})
+        for (int t = 64; t <= 512; t += 32)
+            for (int c : {32, 64, 128}) {
+                b.threads = t;
+                b.tile_i = c;
+                b.persistent = p;
+                pw_status s = pw_batch_build(b, st);
+                if (s == PW_ERR_SHAPE) continue;
+                if (s != PW_OK) return s;
+                float ms = 0;
+                s = pw_time([&] { return pw_batch_launch(b, 0, st); }, st, &ms);
+                if (s != PW_OK) return s;
+                if (ms < best) {
+                    best = ms;
+                    bt = t;
+                    bi = c;
+                    bp = p;
+                }
             }
-        }
     b.threads = bt;
     b.tile_i = bi;
+    b.persistent = bp;
     pw_status s = pw_batch_build(b, st);
     if (s != PW_OK) return s;
     if (best_ms) *best_ms = best;
+    bi = bp ? bi : -bi;
     return pw_cache_store(cache_path, key, bt, bi, best);
 }

@@ -234,13 +234,16 @@ def test_fp32_loop_gradient_vs_fp64(pw):
 
 def test_batch_reorder_keeps_halo_and_stencil_consistent(pw):
     """Changing the CTA size changes the members' tile shapes and hence their
-    work order; the halo fill and the stencil must follow the new order."""
+    work order; the halo fill and the stencil must follow the new order, under
+    either tile schedule."""
     members = [(24, 40, 160, 30.0, 1), (56, 16, 64, 60.0, 2), (40, 40, 97, 45.0, 3),
                (16, 72, 130, 80.0, 4), (48, 24, 70, 25.0, 5), (8, 8, 150, 99.0, 6)]
     b, meshes, fields, sources, host = build_batch(pw, members)
     want = [[m.interior(s).clone() for s in m.advect(*f)] for m, f in zip(meshes, fields)]
     halos = [[t.clone() for t in f] for f in fields]
-    for threads, tile_i in ((128, 16), (512, 64), (256, 8), (384, 32)):
+    for persistent, threads, tile_i in ((1, 128, 16), (1, 512, 64), (0, 256, 8), (0, 384, 32), (0, 96, 64),
+                                        (1, 224, 128)):
+        b.set_schedule(persistent)
         b.set_tile(threads, tile_i)
         for f in fields:
             for t in f:
@@ -255,6 +258,6 @@ def test_batch_reorder_keeps_halo_and_stencil_consistent(pw):
         assert b.status() == 0
         for m, f, h, s, w in zip(meshes, fields, halos, sources, want):
             for t, x in zip(f, h):
-                assert torch.equal(t[:, :, :m.nz], x[:, :, :m.nz]), (threads, tile_i)
+                assert torch.equal(t[:, :, :m.nz], x[:, :, :m.nz]), (persistent, threads, tile_i)
             for t, x in zip(s, w):
-                assert torch.equal(m.interior(t), x), (threads, tile_i)
+                assert torch.equal(m.interior(t), x), (persistent, threads, tile_i)
