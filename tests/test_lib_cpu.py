@@ -54,8 +54,18 @@ def test_null_arguments_rejected(lib):
     assert c.pw_mesh_layout(z, None, None, None, None) == lib.PW_ERR_ARG
     assert c.pw_mesh_set_tile(z, 8, 32) == lib.PW_ERR_ARG
     assert c.pw_advect_batched(z, 0, z) == lib.PW_ERR_ARG
+    assert c.pw_batch_set_schedule(z, 1, z) == lib.PW_ERR_ARG
+    assert c.pw_advect_step(z, *([z] * 6), 0.5, z) == lib.PW_ERR_ARG
+    arr = (ctypes.c_void_p * 1)()
+    assert c.pw_advect_scalars(z, z, z, z, 1, arr, arr, 0, z) == lib.PW_ERR_ARG
+    assert c.pw_pipeline_create(z, 0, ctypes.byref(ctypes.c_void_p())) == lib.PW_ERR_ARG
+    assert c.pw_pipeline_sync(z) == lib.PW_ERR_ARG
+    assert c.pw_pipeline_slab(z, None, None) == lib.PW_ERR_ARG
+    assert c.pw_advect_host(z, *([z] * 6), 0, None, None, z) == lib.PW_ERR_ARG
+    assert "pipeline" in lib.last_error()
     lib.pw_mesh_destroy(z)   # NULL is allowed
     lib.pw_batch_destroy(z)
+    lib.pw_pipeline_destroy(z)
 
 
 def test_bad_descriptors_rejected(lib):
