@@ -225,6 +225,9 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     int kc_one = (m->nz + unit - 1) / unit * unit;
     g.kc = (kc_one + 2 * g.h <= 256) ? kc_one : 128;
     g.kb = g.kc + 2 * g.h;
+    // rows per CTA: as asked, but no more than 512 threads (long columns)
+    tile_j = tile_j < 512 / (g.kc / KV) ? tile_j : 512 / (g.kc / KV);
+    if (tile_j < 1) tile_j = 1;
     g.tj = tile_j;
     g.ti = tile_i;
     g.ns = ns;

@@ -60,6 +60,8 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
     int kc_one = (m->nz + unit - 1) / unit * unit;
     g.kc = (kc_one + 2 * g.h <= 256) ? kc_one : 128;
     g.kb = g.kc + 2 * g.h;
+    // rows per CTA: as asked, but no more than 512 threads (long columns)
+    tile_j = std::max(1, std::min(tile_j, 512 / (g.kc / KV)));
     g.tj = tile_j;
     g.ti = tile_i;
     g.ns = ns;

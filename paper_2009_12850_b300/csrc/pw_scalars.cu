@@ -256,6 +256,9 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     const int kc_max = sizeof(TS) == 8 ? 64 : 128;  // keeps a slot of a few scalars small
     g.kc = kc_one <= kc_max ? kc_one : kc_max;
     g.kb = g.kc + 2 * g.h;
+    // rows per CTA: as asked, but no more than 512 threads (long columns)
+    tile_j = tile_j < 512 / (g.kc / KV) ? tile_j : 512 / (g.kc / KV);
+    if (tile_j < 1) tile_j = 1;
     g.tj = tile_j;
     g.ti = tile_i;
     g.ns = NS;
