@@ -57,7 +57,7 @@ pw_adjoint_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__
     const int j = j0 + tj;
     const CUtensorMap *maps[6] = {&mu, &mv, &mw, &mgu, &mgv, &mgw};
 
-    if (pw_status_failed(status)) return;  // sticky failure: do nothing until cleared
+    if (pw_cta_failed(status)) return;  // sticky failure: do nothing until cleared
     if (threadIdx.x == 0) {
         for (int f = 0; f < 6; f++) pw_prefetch_map(maps[f]);
         for (int s = 0; s < g.ns; s++) pw_mbar_init(&bars[s], 1);

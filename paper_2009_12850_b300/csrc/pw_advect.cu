@@ -14,7 +14,7 @@ pw_advect_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
                 TO *__restrict__ sw, const TC *__restrict__ coef, const PwGeom g, int beta,
                 int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    if (pw_status_failed(status)) return;  // sticky failure: do nothing until cleared
+    if (pw_cta_failed(status)) return;  // sticky failure: do nothing until cleared
     pw_march_tile<TS, TC, TO, KV, PW_MARCH_NS>(&mu, &mv, &mw, su, sv, sw, coef, g, beta, status,
                                                smem_raw, blockIdx.x * g.tj, blockIdx.y * g.ti,
                                                blockIdx.z * g.kc);
@@ -28,7 +28,7 @@ pw_step_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CU
               TS *__restrict__ wn, const TC *__restrict__ coef, const PwGeom g, double dt,
               int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    if (pw_status_failed(status)) return;
+    if (pw_cta_failed(status)) return;
     pw_march_tile<TS, TC, TS, KV, PW_MARCH_NS, true>(&mu, &mv, &mw, un, vn, wn, coef, g, 0, status, smem_raw,
                                                      blockIdx.x * g.tj, blockIdx.y * g.ti, blockIdx.z * g.kc, dt);
 }

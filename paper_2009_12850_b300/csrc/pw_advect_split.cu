@@ -60,7 +60,7 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     const int kbase = k0 + 2 * tk, kk = 2 + 2 * tk, j = j0 + tj;
     const int fs = g.field_stride;
 
-    if (pw_status_failed(status)) return;
+    if (pw_cta_failed(status)) return;
     if (tid == 0) {
         pw_prefetch_map(&mu);
         pw_prefetch_map(&mv);

@@ -72,7 +72,7 @@ pw_batch_kernel(const PwBatchMember *__restrict__ members, int n, int total_tile
             if (pass > 0) return;
             t = blockIdx.x;
         }
-        if (t >= total_tiles || pw_status_failed(status)) return;
+        if (t >= total_tiles || pw_cta_failed(status)) return;
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;

@@ -144,6 +144,19 @@ __device__ __forceinline__ bool pw_status_failed(const int *status) {
     return *reinterpret_cast<const volatile int *>(status) != 0;
 }
 
+// The same test taken once per CTA: thread 0 reads the word and shares the
+// answer, so every thread takes the same branch (a CTA whose threads left at
+// different points could no longer meet at a later barrier).  Contains CTA
+// barriers: call it from every thread of the CTA.
+__device__ __forceinline__ bool pw_cta_failed(const int *status) {
+    __shared__ int flag;
+    if (threadIdx.x == 0) flag = pw_status_failed(status);
+    __syncthreads();
+    const bool f = flag != 0;
+    __syncthreads();  // the next call may overwrite the flag
+    return f;
+}
+
 __device__ __forceinline__ void pw_tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
                                                int c2, uint64_t *bar) {
     asm volatile(

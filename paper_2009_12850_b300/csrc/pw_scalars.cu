@@ -36,46 +36,9 @@ struct PwScalarGeom {
     int n;        // scalars in the launch
 };
 
-// two levels per thread for the 4-byte and 2-byte storage types
-template <typename TC>
-struct SlabLoad<float, TC, 2> {
-    static __device__ __forceinline__ void run(const float *p, TC *o) {
-        const float2 a = *reinterpret_cast<const float2 *>(p);
-        o[0] = a.x; o[1] = a.y;
-    }
-};
-template <typename TC>
-struct SlabLoad<__nv_bfloat16, TC, 2> {
-    static __device__ __forceinline__ void run(const __nv_bfloat16 *p, TC *o) {
-        const uint32_t a = *reinterpret_cast<const uint32_t *>(p);
-        o[0] = __uint_as_float(a << 16);  // bf16 -> f32 is exact
-        o[1] = __uint_as_float(a & 0xffff0000u);
-    }
-};
-
 template <typename TS, typename TC, int KV>
 __device__ __forceinline__ void pw_slab(const TS *row, int kk, TC (&x)[KV]) {
     SlabLoad<TS, TC, KV>::run(row + kk, x);
-}
-
-// stores of KV results; 8-byte vectors for two floats
-template <typename TO, int KV>
-__device__ __forceinline__ void pw_scalar_store(TO *p, const TO (&r)[KV], int nvalid, int beta) {
-    if constexpr (sizeof(TO) == 4 && KV == 2) {
-        if (nvalid >= 2) {
-            float2 val = make_float2(r[0], r[1]);
-            if (beta) {
-                const float2 old = *reinterpret_cast<const float2 *>(p);
-                val.x += old.x;
-                val.y += old.y;
-            }
-            *reinterpret_cast<float2 *>(p) = val;
-        } else {
-            p[0] = beta ? p[0] + r[0] : r[0];
-        }
-    } else {
-        pw_store<TO, KV>(p, r, nvalid, beta);
-    }
 }
 
 // GMAX: most scalars a CTA carries (their x window lives in registers)
@@ -85,7 +48,7 @@ pw_scalar_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
                 const __grid_constant__ CUtensorMap mw, const __grid_constant__ PwScalarSet set,
                 const TC *__restrict__ coef, const PwScalarGeom sg, int beta, int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    if (pw_status_failed(status)) return;
+    if (pw_cta_failed(status)) return;
     const PwGeom &g = sg.g;
     const int kchunk = blockIdx.z % sg.nkc, grp = blockIdx.z / sg.nkc;
     const int s0 = grp * sg.group;
@@ -222,7 +185,7 @@ pw_scalar_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
                         x = x - c2[m] * wC[m + 1] * pC[m + 2];
                         r[m] = (TO)x;
                     }
-                    pw_scalar_store<TO, KV>(reinterpret_cast<TO *>(set.out[s0 + s]) + off, r, nvalid, beta);
+                    pw_store<TO, KV>(reinterpret_cast<TO *>(set.out[s0 + s]) + off, r, nvalid, beta);
                 }
 #pragma unroll
                 for (int m = 0; m < KV; m++) pM[s][m] = pC[m + 1];

@@ -43,7 +43,7 @@ pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
                        const __grid_constant__ CUtensorMap mw, const __grid_constant__ PwScalarSplitSet set,
                        const float *__restrict__ cs, const PwScalarSplitGeom g, int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    if (pw_status_failed(status)) return;
+    if (pw_cta_failed(status)) return;
     const int kchunk = blockIdx.z % g.nkc, grp = blockIdx.z / g.nkc;
     const int s0 = grp * g.group;
     const int G = min(g.group, g.n - s0);
