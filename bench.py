@@ -162,11 +162,23 @@ def whole_job_rate(points_per_rank, world, steps, seconds):
     return world * points_per_rank * steps / seconds
 
 
+def spin_up(fn, seconds=0.3):
+    """Run fn until `seconds` of device work have passed, so that a short timed
+    region does not start on a GPU whose clocks dropped while the host was
+    preparing inputs."""
+    import torch
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        fn()
+        torch.cuda.synchronize()
+
+
 def time_steps(step, steps, warmup, world, events_for=None):
     """W untimed steps, then exactly K timed steps between barriers and
     synchronisations; returns (total seconds of the slowest rank, per-launch ms
     of the kernel recorded by step())."""
     import torch
+    spin_up(lambda: step(None), 0.25)  # clocks at their working level first
     for _ in range(warmup):
         step(None)
     torch.cuda.synchronize()
@@ -279,7 +291,8 @@ def run_gpu(args):
         rm = [float(sums[q, 2] / sums[q, 3]) for q in range(3)]
         extras["residuals"] = {"ms_per_call": round(dt * 1e3, 3), "R_E": re, "R_M": rm}
 
-    for name, fn in (("scalars", lambda: bench_scalars(args, world, hbm)),
+    for name, fn in (("small_latency", lambda: bench_small_latency(args, world)),
+                     ("scalars", lambda: bench_scalars(args, world, hbm)),
                      ("paper_strong_f32", lambda: bench_paper_strong(args, world, hbm)),
                      ("fused_step", lambda: bench_fused_step(args, world, hbm)),
                      ("batched", lambda: bench_batched(args, world, hbm)),
@@ -436,6 +449,46 @@ def bench_scalars(args, world, hbm):
     return out
 
 
+def bench_small_latency(args, world):
+    """The paper's weak-scaling local domain, 64 x 64 x 64 (262,144 points,
+    12.6 MB of FP64 fields: L2-resident), as latency per step: halo fill +
+    stencil launched eagerly, and the same two launches captured in a CUDA
+    graph and replayed."""
+    import torch
+    from paper_2009_12850_b300 import api
+    wl = synthetic.SMALL
+    f = synthetic.fields_for(wl)
+    out = {"workload": wl.name, "points": wl.points, "note": "L2-resident: latency, not a roofline fraction"}
+    for dtype in ("f64", "f32"):
+        m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype)
+        U = [m.from_interior(a) for a in f]
+        S = [m.empty_out() for _ in range(3)]
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                m.halo(*U, stream=side)
+                m.advect(*U, *S, stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            m.halo(*U)
+            m.advect(*U, *S)
+        stream = torch.cuda.current_stream()
+
+        def eager(rec):
+            m.halo(*U, stream=stream)
+            m.advect(*U, *S, stream=stream)
+        steps = max(200, args.steps * 10)
+        te, _ = time_steps(eager, steps, 5, world)
+        tg, _ = time_steps(lambda rec: graph.replay(), steps, 5, world)
+        assert m.device_status() == 0
+        out[dtype] = {"us_per_step_eager": round(te / steps * 1e6, 2), "us_per_step_graph": round(tg / steps * 1e6, 2),
+                      "points_per_s_graph": world * wl.points * steps / tg}
+        del graph, m, U, S
+    return out
+
+
 def bench_fused_step(args, world, hbm):
     """One forward Euler timestep of the wind on 1024 x 1024 x 128: the fused
     stencil + update (pw_advect_step, halos of the new state written in the same
@@ -524,9 +577,8 @@ def bench_adjoint_loop(args):
             L = autograd.source_energy_loss(m, *U, dt=dt, steps=steps, checkpoint_every=every)
             L.backward()
             return L, U
-        L, U = one()
-        torch.cuda.synchronize()
-        reps = 3 if dtype == "f32" else 1
+        spin_up(one)
+        reps = 10 if dtype == "f32" else 3
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
@@ -637,7 +689,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="only the headline and e2e")
     ap.add_argument("--extras", default=None,
-                    help="comma list of extra rows to run (default all): f32, bf16, f64_native, residuals, scalars, "
+                    help="comma list of extra rows to run (default all): f32, bf16, f64_native, residuals, "
+                         "small_latency, scalars, "
                          "paper_strong_f32, fused_step, batched, adjoint_loop, precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

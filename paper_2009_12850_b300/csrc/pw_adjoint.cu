@@ -229,6 +229,7 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     tile_j = tile_j < 512 / (g.kc / KV) ? tile_j : 512 / (g.kc / KV);
     if (tile_j < 1) tile_j = 1;
     g.tj = tile_j;
+    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
     g.ti = tile_i;
     g.ns = ns;
     g.plane_elems = (tile_j + 2) * g.kb;

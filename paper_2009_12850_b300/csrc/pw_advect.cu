@@ -63,6 +63,7 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
     // rows per CTA: as asked, but no more than 512 threads (long columns)
     tile_j = std::max(1, std::min(tile_j, 512 / (g.kc / KV)));
     g.tj = tile_j;
+    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
     g.ti = tile_i;
     g.ns = ns;
     g.plane_elems = (tile_j + 2) * g.kb;

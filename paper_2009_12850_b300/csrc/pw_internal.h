@@ -60,6 +60,16 @@ pw_status pw_make_field_map(CUtensorMap *map, const void *base, pw_dtype dtype, 
                             int nzp, int kdim, int kbox, int rows);
 static inline int pw_kdim(int nz, int field) { return field == 2 ? (nz > 1 ? nz - 1 : 1) : nz; }
 
+// Columns marched per CTA for a launch whose other grid dimensions hold
+// `ctas_per_column_tile` CTAs: the requested tile_i, halved (down to 4) while
+// the grid would not fill one wave of the GPU (small domains would otherwise
+// leave SMs idle and march long columns serially).
+static inline int pw_fit_tile_i(const pw_mesh *m, int tile_i, long ctas_per_column_tile) {
+    const long wave = 4L * m->num_sms;  // typical resident CTAs of the x-march kernels
+    while (tile_i > 4 && ctas_per_column_tile * ((m->nx + tile_i - 1) / tile_i) < wave) tile_i = (tile_i + 1) / 2;
+    return tile_i;
+}
+
 // launchers (pw_advect.cu / pw_adjoint.cu)
 pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const void *w,
                            void *su, void *sv, void *sw, int beta, cudaStream_t st,

@@ -233,6 +233,7 @@ pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v
     const int kc_one = (m->nz + 1) / 2 * 2;
     g.kc = kc_one <= 64 ? kc_one : 64;
     g.kb = g.kc + 4;
+    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
     g.ti = tile_i;
     const int plane_elems = (tile_j + 2) * g.kb;
     g.field_stride = (plane_elems + 15) / 16 * 16;  // 128-byte aligned planes
