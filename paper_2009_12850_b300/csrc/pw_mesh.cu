@@ -102,34 +102,38 @@ pw_status pw_make_field_map(CUtensorMap *map, const void *base, pw_dtype dtype, 
 }
 
 // ---------------------------------------------------------------------------
-// A1: vertical grid and coefficients in FP64 (one thread: nz is small and the
-// prefix sum is sequential)
+// A1: vertical grid and coefficients in FP64, one CTA, levels in parallel.
+// zf(k) is summed by thread k over dz(0..k) in increasing order, so every
+// prefix is rounded exactly as a sequential running sum would round it.
 // ---------------------------------------------------------------------------
 __global__ void pw_coeffs_kernel(int nz, const double *dz_in, const double *rn_in,
                                  const double *rw_in, int have_dz, int have_rn, int have_rw,
                                  double rho0, double H, double *c64, float *c32) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (blockIdx.x != 0) return;
     double *dz = c64, *zf = c64 + nz, *zn = c64 + 2 * nz, *dzn = c64 + 3 * nz;
     double *rn = c64 + 4 * nz, *rw = c64 + 5 * nz;
     double *t1 = c64 + 6 * nz, *t2 = c64 + 7 * nz, *d1 = c64 + 8 * nz, *d2 = c64 + 9 * nz;
     double *wuv = c64 + 10 * nz, *ww = c64 + 11 * nz;
-    for (int k = 0; k < nz; k++) {
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         if (have_dz) dz[k] = dz_in[k];
         else if (nz == 1) dz[k] = 10.0;
         else dz[k] = 10.0 * pow(4.0, (double)k / (double)(nz - 1));
     }
-    double z = 0.0;
-    for (int k = 0; k < nz; k++) {
-        z += dz[k];
+    __syncthreads();
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        double z = 0.0;
+        for (int q = 0; q <= k; q++) z += dz[q];
         zf[k] = z;
         zn[k] = z - 0.5 * dz[k];
     }
-    for (int k = 0; k < nz; k++) dzn[k] = (k < nz - 1) ? zn[k + 1] - zn[k] : 0.0;
-    for (int k = 0; k < nz; k++) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        dzn[k] = (k < nz - 1) ? zn[k + 1] - zn[k] : 0.0;
         rn[k] = have_rn ? rn_in[k] : rho0 * exp(-zn[k] / H);
         rw[k] = have_rw ? rw_in[k] : rho0 * exp(-zf[k] / H);
     }
-    for (int k = 0; k < nz; k++) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         double below = (k == 0) ? rho0 : rw[k - 1];
         t1[k] = 0.25 * below / (rn[k] * dz[k]);
         t2[k] = 0.25 * rw[k] / (rn[k] * dz[k]);
@@ -155,10 +159,10 @@ __global__ void pw_coeffs_kernel(int nz, const double *dz_in, const double *rn_i
 // r' = 1/(rho_w dzn) (0 on the lid face), each stored as hi + lo floats for
 // levels -2 .. nz+1 (0 outside 0..nz-1), followed by tcx and tcy.
 __global__ void pw_coeffs_split_kernel(int nz, const double *c64, double tcx, double tcy, float *cs) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (blockIdx.x != 0) return;
     const double *dz = c64, *dzn = c64 + 3 * nz, *rn = c64 + 4 * nz, *rw = c64 + 5 * nz;
     const int n = nz + 4;
-    for (int q = 0; q < n; q++) {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
         const int k = q - 2;
         const bool in = k >= 0 && k < nz;
         double v[4];
@@ -172,6 +176,7 @@ __global__ void pw_coeffs_split_kernel(int nz, const double *c64, double tcx, do
             cs[(2 * a + 1) * n + q] = (float)(v[a] - (double)h);
         }
     }
+    if (threadIdx.x != 0) return;
     const double t[2] = {tcx, tcy};
     for (int a = 0; a < 2; a++) {
         const float h = (float)t[a];
@@ -259,11 +264,11 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
         if (d->rho_n && (e = cudaMemcpyAsync(tmp + nz, d->rho_n, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if (d->rho_w && (e = cudaMemcpyAsync(tmp + 2 * nz, d->rho_w, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(m->status, 0, 2 * sizeof(int), st)) != cudaSuccess) break;
-        pw_coeffs_kernel<<<1, 32, 0, st>>>(nz, tmp, tmp + nz, tmp + 2 * nz, d->dz != nullptr,
+        pw_coeffs_kernel<<<1, 256, 0, st>>>(nz, tmp, tmp + nz, tmp + 2 * nz, d->dz != nullptr,
                                            d->rho_n != nullptr, d->rho_w != nullptr, rho0, H,
                                            m->coef64, m->coef32);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
-        pw_coeffs_split_kernel<<<1, 32, 0, st>>>(nz, m->coef64, m->tcx, m->tcy, m->coefsplit);
+        pw_coeffs_split_kernel<<<1, 256, 0, st>>>(nz, m->coef64, m->tcx, m->tcy, m->coefsplit);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         e = cudaStreamSynchronize(st);
     } while (0);
