@@ -490,13 +490,16 @@ def bench_small_latency(args, world):
 
 
 def bench_fused_step(args, world, hbm):
-    """One forward Euler timestep of the wind on 1024 x 1024 x 128: the fused
-    stencil + update (pw_advect_step, halos of the new state written in the same
-    pass) against halo fill + pw_advect + pw_euler."""
+    """One forward Euler timestep on 1024 x 1024 x 128: the fused stencil +
+    update (pw_advect_step, halos of the new state written in the same pass)
+    against halo fill + pw_advect + pw_euler; and the whole advection step of
+    the wind with theta + 5 q (pw_advect_step + pw_advect_scalars_step against
+    halos + both stencils + three pw_euler passes)."""
     import torch
     from paper_2009_12850_b300 import api
     out = {"workload": WL.name, "dt": 0.5}
     f = synthetic.fields_for(WL)
+    phis = synthetic.scalar_fields(WL.nx, WL.ny, WL.nz, 6, WL.seed + 100)
     pts = WL.points
     for dtype in ("f64", "f32"):
         m = api.Mesh(WL.nx, WL.ny, WL.nz, WL.dx, WL.dy, dtype=dtype)
@@ -522,7 +525,35 @@ def bench_fused_step(args, world, hbm):
                       "unit": UNIT, "fused_ms": round(tf / steps * 1e3, 4), "unfused_ms": round(tu / steps * 1e3, 4),
                       "speedup": round(tu / tf, 3), "fused_bytes_per_point": 6 * es,
                       "unfused_bytes_per_point": 15 * es}
-        del m, A, B, S, cur
+        # the whole advection step of the wind and theta + 5 q (old wind for all)
+        P = [m.from_interior(a) for a in phis]
+        Q = [m.empty() for _ in range(6)]
+        pcur = [P, Q]
+
+        def fused_all(rec):
+            m.step(*cur[0], *cur[1], dt=0.5)
+            m.step_scalars(*cur[0], pcur[0], pcur[1], dt=0.5)
+            cur.reverse()
+            pcur.reverse()
+        tfa, _ = time_steps(fused_all, steps, 3, world)
+        SP = [m.empty_out() for _ in range(6)]
+
+        def unfused_all(rec):
+            m.halo(*A)
+            m.halo(*P[:3])
+            m.halo(*P[3:])
+            m.advect(*A, *S)
+            m.advect_scalars(*A, P, SP)
+            m.euler(*A, *S, 0.5)
+            m.euler(*P[:3], *SP[:3], 0.5)
+            m.euler(*P[3:], *SP[3:], 0.5)
+        tua, _ = time_steps(unfused_all, steps, 3, world)
+        assert m.device_status() == 0
+        out[dtype]["wind_theta_5q"] = {"fused_ms": round(tfa / steps * 1e3, 4),
+                                       "unfused_ms": round(tua / steps * 1e3, 4), "speedup": round(tua / tfa, 3),
+                                       "fused_bytes_per_point": (6 + 15) * es,
+                                       "unfused_bytes_per_point": (15 + 3 + 6 * 5) * es}
+        del m, A, B, S, cur, P, Q, SP, pcur
         torch.cuda.empty_cache()
     return out
 

@@ -215,6 +215,16 @@ pw_status pw_advect_step(const pw_mesh *mesh, const void *u, const void *v, cons
 pw_status pw_advect_scalars(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
                             const void *const *phi, void *const *sphi, int beta, void *stream);
 
+/* The forward Euler step of the scalars fused into their stencil (the step-fields
+ * update of section 3 on the device for theta and q): with halos filled,
+ *   phin[a] = phi[a] + dt s(phi[a]; u, v, w)
+ * on interior points and on their periodic halo images (ready for the next
+ * step), s as in pw_advect_scalars, the update one FMA in the compute
+ * precision.  phin[a] have the mesh dtype (BF16 results are rounded to bf16).
+ * Same argument rules as pw_advect_scalars; dt must be finite. */
+pw_status pw_advect_scalars_step(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
+                                 const void *const *phi, void *const *phin, double dt, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Fields in host memory: the step with its copies overlapped (the hybrid
  * offload of sections 3 and 3.1, where u, v, w go to the device every timestep

@@ -60,6 +60,7 @@ _SIGS = {
     "pw_halo_fold": ([_vp, _vp, _vp, _vp, _vp], _i),
     "pw_advect": ([_vp] + [_vp] * 6 + [_i, _vp], _i),
     "pw_advect_step": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
+    "pw_advect_scalars_step": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _vp], _i),
     "pw_advect_scalars": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp], _i),
     "pw_pipeline_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
     "pw_pipeline_destroy": ([_vp], None),
@@ -215,6 +216,11 @@ def pw_advect_host(p, u, v, w, su, sv, sw, beta, on_slab, user, stream):
     """on_slab: a SLAB_FN instance or None (the caller keeps it alive)."""
     fn = ctypes.cast(on_slab, _vp) if on_slab is not None else None
     check(_c.pw_advect_host(p, u, v, w, su, sv, sw, int(beta), fn, user, stream), "pw_advect_host")
+
+
+def pw_advect_scalars_step(mesh, u, v, w, phi, phin, dt, stream):
+    check(_c.pw_advect_scalars_step(mesh, u, v, w, len(phi), _ptrs(phi), _ptrs(phin), float(dt), stream),
+          "pw_advect_scalars_step")
 
 
 def pw_advect_adjoint(mesh, u, v, w, gsu, gsv, gsw, gu, gv, gw, alpha, beta, stream):

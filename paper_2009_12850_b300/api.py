@@ -149,6 +149,18 @@ class Mesh:
                             [self._check(s, "sphi", True) for s in sources], beta, _stream(stream))
         return sources
 
+    def step_scalars(self, u, v, w, phis, outs=None, dt=1.0, stream=None):
+        """Fused forward Euler step of the scalars: outs[a] = phis[a] + dt s(phis[a]),
+        halos included; returns outs."""
+        phis = list(phis)
+        outs = [self.empty() for _ in phis] if outs is None else list(outs)
+        if len(outs) != len(phis):
+            raise ValueError("one output tensor per scalar")
+        L.pw_advect_scalars_step(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                                 [self._check(p, "phi") for p in phis], [self._check(o, "phin") for o in outs],
+                                 dt, _stream(stream))
+        return outs
+
     def adjoint(self, u, v, w, gsu, gsv, gsw, gu=None, gv=None, gw=None, alpha=1.0, beta=0, stream=None):
         gu = self.zeros() if gu is None else gu
         gv = self.zeros() if gv is None else gv

@@ -242,7 +242,7 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     int threads = (g.kc / KV) * tile_j;
     if (threads > 512) return pw_fail(PW_ERR_SHAPE, "adjoint tile needs %d threads", threads);
     size_t smem = (size_t)ns * 6 * g.field_stride * sizeof(TS) + (size_t)ns * sizeof(uint64_t);
-    if (smem > 227 * 1024) return pw_fail(PW_ERR_SHAPE, "adjoint tile needs %zu bytes of shared memory", smem);
+    if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "adjoint tile needs %zu bytes of shared memory", smem);
     CUtensorMap maps[6];
     for (int q = 0; q < 6; q++) {
         pw_status s = pw_make_field_map(&maps[q], in[q], m->dtype, m->nx, m->ny, m->nzp, pw_kdim(m->nz, q % 3),

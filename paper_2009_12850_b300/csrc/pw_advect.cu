@@ -78,7 +78,7 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
         return pw_fail(PW_ERR_SHAPE, "tile_j=%d needs %d threads (> 512) for k chunk %d", tile_j,
                        threads, g.kc);
     size_t smem = (size_t)ns * 3 * g.field_stride * sizeof(TS) + (size_t)ns * sizeof(uint64_t);
-    if (smem > 227 * 1024) return pw_fail(PW_ERR_SHAPE, "tile needs %zu bytes of shared memory", smem);
+    if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "tile needs %zu bytes of shared memory", smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
     for (int q = 0; q < 3; q++) {

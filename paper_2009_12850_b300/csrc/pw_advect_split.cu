@@ -304,7 +304,7 @@ static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v,
     static_assert(NS * sizeof(uint64_t) <= 64, "barrier slot");
     const size_t smem = (size_t)NS * 3 * g.field_stride * 8 + 64 +
                         ((size_t)(g.kc / 2) * 6 + 2) * sizeof(float4);
-    if (smem > 227 * 1024) return pw_fail(PW_ERR_SHAPE, "split kernel needs %zu bytes of shared memory", smem);
+    if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "split kernel needs %zu bytes of shared memory", smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
     for (int q = 0; q < 3; q++) {

@@ -208,7 +208,7 @@ static pw_status pw_batch_build(pw_batch_impl &b, cudaStream_t st) {
             }
         }
     }
-    if (smem > 227 * 1024) return pw_fail(PW_ERR_SHAPE, "batch tile needs %zu bytes of shared memory", smem);
+    if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "batch tile needs %zu bytes of shared memory", smem);
     b.total_tiles = first;
     b.halo_cols = halo;
     b.smem = smem;

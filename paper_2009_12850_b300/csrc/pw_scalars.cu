@@ -41,12 +41,16 @@ __device__ __forceinline__ void pw_slab(const TS *row, int kk, TC (&x)[KV]) {
     SlabLoad<TS, TC, KV>::run(row + kk, x);
 }
 
-// GMAX: most scalars a CTA carries (their x window lives in registers)
-template <typename TS, typename TC, typename TO, int KV, int NS, int GMAX>
+// GMAX: most scalars a CTA carries (their x window lives in registers).
+// STEP: write phi + dt s (the forward Euler step fused into the stencil; phi is
+// the centre value already in registers) in the field type, at the column and
+// at its periodic halo images, instead of the source s.
+template <typename TS, typename TC, typename TO, int KV, int NS, int GMAX, bool STEP = false>
 __global__ void __launch_bounds__(512)
 pw_scalar_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                 const __grid_constant__ CUtensorMap mw, const __grid_constant__ PwScalarSet set,
-                const TC *__restrict__ coef, const PwScalarGeom sg, int beta, int *__restrict__ status) {
+                const TC *__restrict__ coef, const PwScalarGeom sg, int beta, int *__restrict__ status,
+                double dt = 0.0) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (pw_cta_failed(status)) return;
     const PwGeom &g = sg.g;
@@ -123,6 +127,7 @@ pw_scalar_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
         c2[m] = in ? TC(2) * coef[g.nz + k] : TC(0);
     }
     const TC hx = TC(2) * (TC)g.tcx, hy = TC(2) * (TC)g.tcy;
+    const TC tdt = (TC)dt;
     const int L = g.kb;
     const int rS = tjc * L, rC = (tjc + 1) * L, rN = (tjc + 2) * L;
 
@@ -183,9 +188,13 @@ pw_scalar_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
                         x = x + hy * (vS[m] * pS[m] - vC[m] * pN[m]);
                         x = x + c1[m] * wC[m] * pC[m];
                         x = x - c2[m] * wC[m + 1] * pC[m + 2];
-                        r[m] = (TO)x;
+                        r[m] = STEP ? (TO)(pC[m + 1] + tdt * x) : (TO)x;
                     }
-                    pw_store<TO, KV>(reinterpret_cast<TO *>(set.out[s0 + s]) + off, r, nvalid, beta);
+                    if (STEP)
+                        pw_store_images<TO, KV>(reinterpret_cast<TO *>(set.out[s0 + s]), i, j, kbase, r, nvalid,
+                                                g.nx, g.ny, g.si, g.sj);
+                    else
+                        pw_store<TO, KV>(reinterpret_cast<TO *>(set.out[s0 + s]) + off, r, nvalid, beta);
                 }
 #pragma unroll
                 for (int m = 0; m < KV; m++) pM[s][m] = pC[m + 1];
@@ -202,10 +211,10 @@ pw_scalar_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
 // --------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------
-template <typename TS, typename TC, typename TO, int KV>
+template <typename TS, typename TC, typename TO, int KV, bool STEP = false>
 static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
                                    const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
-                                   int tile_j, int tile_i, int group) {
+                                   int tile_j, int tile_i, int group, double dt = 0.0) {
     constexpr int NS = PW_SCALAR_NS;
     PwScalarGeom sg;
     PwGeom &g = sg.g;
@@ -241,7 +250,7 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     // memory (at most PW_SCALAR_GMAX, whose x window is held in registers),
     // then balanced over the groups; fewer groups means fewer reads of the wind
     if (group <= 0) {
-        const long fit = (long)(227 * 1024 - 64) / (long)field_bytes - 3;
+        const long fit = (long)(226 * 1024) / (long)field_bytes - 3;
         group = (int)std::max(1L, std::min((long)std::min(n, PW_SCALAR_GMAX), fit));
         const int ngroups = (n + group - 1) / group;
         group = (n + ngroups - 1) / ngroups;
@@ -251,7 +260,7 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     sg.n = n;
     sg.nkc = (m->nz + g.kc - 1) / g.kc;
     const size_t smem = field_bytes * (size_t)(3 + group) + (size_t)NS * sizeof(uint64_t);
-    if (smem > 227 * 1024)
+    if (smem > 226 * 1024)
         return pw_fail(PW_ERR_SHAPE, "scalars: %d per CTA need %zu bytes of shared memory", group, smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
@@ -268,7 +277,7 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
         if (s != PW_OK) return s;
         set.out[q] = sphi[q];
     }
-    auto kern = pw_scalar_march<TS, TC, TO, KV, NS, PW_SCALAR_GMAX>;
+    auto kern = pw_scalar_march<TS, TC, TO, KV, NS, PW_SCALAR_GMAX, STEP>;
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long ngroups = (n + group - 1) / group;
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
@@ -276,14 +285,14 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");
     const TC *coef = std::is_same<TC, double>::value ? reinterpret_cast<const TC *>(m->coef64 + 6 * m->nz)
                                                      : reinterpret_cast<const TC *>(m->coef32);
-    kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], set, coef, sg, beta, m->status);
+    kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], set, coef, sg, beta, m->status, dt);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
 }
 
 pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
                                   const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
-                                  int tile_j, int tile_i, int group);
+                                  int tile_j, int tile_i, int group, bool step = false, double dt = 0.0);
 
 pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
                                    const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
@@ -304,12 +313,11 @@ pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *
     return pw_fail(PW_ERR_DTYPE, "unknown dtype");
 }
 
-extern "C" pw_status pw_advect_scalars(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
-                                       const void *const *phi, void *const *sphi, int beta, void *stream) {
-    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
-    if (beta != 0 && beta != 1) return pw_fail(PW_ERR_ARG, "beta must be 0 or 1");
+// checks shared by the scalar entry points: pointers, count, no aliasing
+static pw_status pw_check_scalar_args(const void *u, const void *v, const void *w, int n,
+                                      const void *const *phi, void *const *out) {
     if (n < 1 || n > PW_MAX_SCALARS) return pw_fail(PW_ERR_ARG, "n = %d scalars (1..%d)", n, PW_MAX_SCALARS);
-    if (!phi || !sphi) return pw_fail(PW_ERR_ARG, "phi / sphi arrays are NULL");
+    if (!phi || !out) return pw_fail(PW_ERR_ARG, "scalar pointer arrays are NULL");
     const void *wind[3] = {u, v, w};
     const char *wn[3] = {"u", "v", "w"};
     for (int q = 0; q < 3; q++) {
@@ -319,15 +327,53 @@ extern "C" pw_status pw_advect_scalars(const pw_mesh *m, const void *u, const vo
     for (int a = 0; a < n; a++) {
         pw_status s = pw_check_ptr(phi[a], "phi[a]");
         if (s != PW_OK) return s;
-        s = pw_check_ptr(sphi[a], "sphi[a]");
+        s = pw_check_ptr(out[a], "out[a]");
         if (s != PW_OK) return s;
         for (int q = 0; q < 3; q++)
-            if (sphi[a] == wind[q]) return pw_fail(PW_ERR_ARG, "sphi[%d] aliases %s", a, wn[q]);
+            if (out[a] == wind[q]) return pw_fail(PW_ERR_ARG, "output %d aliases %s", a, wn[q]);
         for (int b = 0; b < n; b++) {
-            if (sphi[a] == phi[b]) return pw_fail(PW_ERR_ARG, "sphi[%d] aliases phi[%d]", a, b);
-            if (b > a && sphi[a] == sphi[b]) return pw_fail(PW_ERR_ARG, "sphi[%d] and sphi[%d] alias", a, b);
+            if (out[a] == phi[b]) return pw_fail(PW_ERR_ARG, "output %d aliases phi[%d]", a, b);
+            if (b > a && out[a] == out[b]) return pw_fail(PW_ERR_ARG, "outputs %d and %d alias", a, b);
         }
     }
+    return PW_OK;
+}
+
+extern "C" pw_status pw_advect_scalars(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
+                                       const void *const *phi, void *const *sphi, int beta, void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    if (beta != 0 && beta != 1) return pw_fail(PW_ERR_ARG, "beta must be 0 or 1");
+    pw_status s = pw_check_scalar_args(u, v, w, n, phi, sphi);
+    if (s != PW_OK) return s;
     return pw_launch_advect_scalars(m, u, v, w, n, phi, sphi, beta, (cudaStream_t)stream, m->tile_j,
                                     m->tile_i, 0);
+}
+
+pw_status pw_launch_scalars_step(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
+                                 const void *const *phi, void *const *phin, double dt, cudaStream_t st,
+                                 int tile_j, int tile_i) {
+    switch (m->dtype) {
+        case PW_F64:
+            if (m->algo == PW_ALGO_F64_SPLIT)
+                return pw_launch_scalars_split(m, u, v, w, n, phi, phin, 0, st, tile_j, tile_i, 0, true, dt);
+            return pw_launch_scalars<double, double, double, 2, true>(m, u, v, w, n, phi, phin, 0, st, tile_j,
+                                                                      tile_i, 0, dt);
+        case PW_F32:
+            return pw_launch_scalars<float, float, float, 4, true>(m, u, v, w, n, phi, phin, 0, st, tile_j,
+                                                                   tile_i, 0, dt);
+        case PW_BF16:
+            return pw_launch_scalars<__nv_bfloat16, float, __nv_bfloat16, 4, true>(m, u, v, w, n, phi, phin, 0,
+                                                                                   st, tile_j, tile_i, 0, dt);
+    }
+    return pw_fail(PW_ERR_DTYPE, "unknown dtype");
+}
+
+extern "C" pw_status pw_advect_scalars_step(const pw_mesh *m, const void *u, const void *v, const void *w,
+                                            int n, const void *const *phi, void *const *phin, double dt,
+                                            void *stream) {
+    if (!m) return pw_fail(PW_ERR_ARG, "mesh is NULL");
+    if (!(dt == dt) || dt - dt != 0.0) return pw_fail(PW_ERR_ARG, "dt must be finite");
+    pw_status s = pw_check_scalar_args(u, v, w, n, phi, phin);
+    if (s != PW_OK) return s;
+    return pw_launch_scalars_step(m, u, v, w, n, phi, phin, dt, (cudaStream_t)stream, m->tile_j, m->tile_i);
 }

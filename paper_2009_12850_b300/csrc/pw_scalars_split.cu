@@ -20,6 +20,7 @@
 
 #include "pw_df.cuh"
 #include "pw_internal.h"
+#include "pw_march.cuh"  // pw_store_images
 
 #define PW_SSPLIT_NS 3    // planes i, i+1 and the one in flight
 #define PW_SSPLIT_GMAX 6  // scalars per CTA at most
@@ -27,6 +28,7 @@
 struct PwScalarSplitSet {
     CUtensorMap phi[PW_MAX_SCALARS];
     double *out[PW_MAX_SCALARS];
+    const double *in[PW_MAX_SCALARS];  // the scalars themselves (read exactly by the fused step)
 };
 
 struct PwScalarSplitGeom {
@@ -37,11 +39,14 @@ struct PwScalarSplitGeom {
     long long si, sj;
 };
 
-template <int NS, int TJ, bool BETA, int GMAX>
+// STEP: write phi + dt s (phi read exactly from set.in; the staged planes hold
+// hi/lo pairs) at the column and at its periodic halo images
+template <int NS, int TJ, bool BETA, int GMAX, bool STEP = false>
 __global__ void __launch_bounds__(256)
 pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                        const __grid_constant__ CUtensorMap mw, const __grid_constant__ PwScalarSplitSet set,
-                       const float *__restrict__ cs, const PwScalarSplitGeom g, int *__restrict__ status) {
+                       const float *__restrict__ cs, const PwScalarSplitGeom g, int *__restrict__ status,
+                       double dt = 0.0) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (pw_cta_failed(status)) return;
     const int kchunk = blockIdx.z % g.nkc, grp = blockIdx.z / g.nkc;
@@ -198,16 +203,24 @@ pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
                     const D2 Z = df_sub(df_mul(A, ld2<-1>(pr + rC, kk)), df_mul(B, ld2<1>(pr + rC, kk)));
                     const D2 r = df_add(df_add(X, Y), Z);
                     double a0 = join(lx(r.h), lx(r.l)), a1 = join(ly(r.h), ly(r.l));
-                    double *po = set.out[s0 + s] + off;
-                    if (kbase + 1 < g.nz) {
-                        if (BETA) {
-                            const double2 o = *reinterpret_cast<const double2 *>(po);
-                            a0 += o.x;
-                            a1 += o.y;
-                        }
-                        *reinterpret_cast<double2 *>(po) = make_double2(a0, a1);
+                    if constexpr (STEP) {
+                        const double *px = set.in[s0 + s] + off;
+                        const bool two = kbase + 1 < g.nz;
+                        const double o2[2] = {fma(dt, a0, px[0]), two ? fma(dt, a1, px[1]) : 0.0};
+                        pw_store_images<double, 2>(set.out[s0 + s], i, j, kbase, o2, g.nz - kbase, g.nx, g.ny,
+                                                   g.si, g.sj);
                     } else {
-                        po[0] = BETA ? po[0] + a0 : a0;
+                        double *po = set.out[s0 + s] + off;
+                        if (kbase + 1 < g.nz) {
+                            if (BETA) {
+                                const double2 o = *reinterpret_cast<const double2 *>(po);
+                                a0 += o.x;
+                                a1 += o.y;
+                            }
+                            *reinterpret_cast<double2 *>(po) = make_double2(a0, a1);
+                        } else {
+                            po[0] = BETA ? po[0] + a0 : a0;
+                        }
                     }
                 }
                 pM[s] = pC;
@@ -222,7 +235,7 @@ pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
 
 pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
                                   const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
-                                  int tile_j, int tile_i, int group) {
+                                  int tile_j, int tile_i, int group, bool step, double dt) {
     constexpr int NS = PW_SSPLIT_NS;
     // compiled for 4 or 8 rows of columns per CTA (the nearest of the two is used)
     tile_j = tile_j <= 5 ? 4 : 8;
@@ -247,7 +260,7 @@ pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v
     const size_t field_bytes = (size_t)NS * g.field_stride * 8;
     const size_t fixed = 64 + ((size_t)(g.kc / 2) * 3 + 2) * sizeof(float4);
     if (group <= 0) {
-        const long fit = (long)(227 * 1024 - fixed) / (long)field_bytes - 3;
+        const long fit = (long)(226 * 1024 - fixed) / (long)field_bytes - 3;
         group = (int)std::max(1L, std::min((long)std::min(n, PW_SSPLIT_GMAX), fit));
         const int ngroups = (n + group - 1) / group;
         group = (n + ngroups - 1) / ngroups;
@@ -257,7 +270,7 @@ pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v
     g.n = n;
     g.nkc = (m->nz + g.kc - 1) / g.kc;
     const size_t smem = field_bytes * (size_t)(3 + group) + fixed;
-    if (smem > 227 * 1024)
+    if (smem > 226 * 1024)
         return pw_fail(PW_ERR_SHAPE, "scalar split kernel needs %zu bytes of shared memory", smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
@@ -273,16 +286,19 @@ pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v
                                         tile_j + 2);
         if (s != PW_OK) return s;
         set.out[q] = (double *)sphi[q];
+        set.in[q] = (const double *)phi[q];
     }
     constexpr int GM = PW_SSPLIT_GMAX;
-    auto kern = tile_j == 4 ? (beta ? pw_scalar_split_kernel<NS, 4, true, GM> : pw_scalar_split_kernel<NS, 4, false, GM>)
-                            : (beta ? pw_scalar_split_kernel<NS, 8, true, GM> : pw_scalar_split_kernel<NS, 8, false, GM>);
+    auto kern = step ? (tile_j == 4 ? pw_scalar_split_kernel<NS, 4, false, GM, true>
+                                    : pw_scalar_split_kernel<NS, 8, false, GM, true>)
+                     : tile_j == 4 ? (beta ? pw_scalar_split_kernel<NS, 4, true, GM> : pw_scalar_split_kernel<NS, 4, false, GM>)
+                                   : (beta ? pw_scalar_split_kernel<NS, 8, true, GM> : pw_scalar_split_kernel<NS, 8, false, GM>);
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long ngroups = (n + group - 1) / group;
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)(g.nkc * ngroups));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");
-    kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], set, m->coefsplit, g, m->status);
+    kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], set, m->coefsplit, g, m->status, dt);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
 }

@@ -1,7 +1,8 @@
-"""GPU tests of the fused forward Euler step (pw_advect_step): the new state
-against one Euler step of the FP64 oracle, bit for bit against the unfused
-pw_advect + pw_euler sequence, halo images, the lid, several steps in a row,
-and the argument checks."""
+"""GPU tests of the fused forward Euler steps (pw_advect_step for the wind,
+pw_advect_scalars_step for theta and q): the new state against one Euler step
+of the FP64 oracle, bit for bit against the unfused stencil + pw_euler
+sequence, halo images, the lid, several steps in a row, and the argument
+checks."""
 import numpy as np
 import pytest
 import torch
@@ -130,4 +131,65 @@ def test_step_argument_errors(pw):
         m.step(*U, N[0], N[0], N[2])
     with pytest.raises(L.PWError):
         m.step(*U, *N, dt=float("nan"))
+    assert m.device_status() == 0
+
+
+# --------------------------------------------------------------------------
+# the fused step of the scalars (theta, q)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(40, 24, 16), (5, 7, 1), (1, 9, 6), (37, 23, 13), (50, 17, 130)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("dtype,algo", KINDS)
+def test_scalar_step_matches_oracle(pw, shape, dtype, algo):
+    nx, ny, nz = shape
+    dt = 0.6
+    m = pw.Mesh(nx, ny, nz, 45.0, 30.0, dtype=dtype, algo=algo)
+    f = rounded(synthetic.wind_fields(nx, ny, nz, 71), dtype)
+    phis = rounded(synthetic.scalar_fields(nx, ny, nz, 3, 72), dtype)
+    U = [m.from_interior(a) for a in f]
+    P = [m.from_interior(a) for a in phis]
+    N = m.step_scalars(*U, P, dt=dt)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    c = oracle.Coeffs(nz, 45.0, 30.0)
+    tol, ulp = {"f64": (TOL_F64, 2.0 ** -52), "f32": (TOL_F32_COND, 2.0 ** -23), "bf16": (TOL_F32_COND, 2.0 ** -8)}[dtype]
+    for q, phi in enumerate(phis):
+        s, cond = oracle.advect_scalar(c, *f, phi, want_cond=True)
+        r = phi + dt * s
+        got = m.interior(N[q]).double().cpu().numpy()
+        bound = tol * dt * cond + ulp * (np.abs(phi) + np.abs(r))
+        err = np.abs(got - r)
+        assert np.all(err <= bound), (q, float((err / np.maximum(bound, 1e-300)).max()))
+        h = N[q].clone()
+        m.halo(h)
+        torch.cuda.synchronize()
+        assert torch.equal(h[:, :, :nz], N[q][:, :, :nz])
+
+
+@pytest.mark.parametrize("dtype,algo", [("f64", "split"), ("f64", "native"), ("f32", "auto")])
+def test_scalar_step_equals_advect_then_euler(pw, dtype, algo):
+    nx, ny, nz = 33, 21, 19
+    m = pw.Mesh(nx, ny, nz, 40.0, dtype=dtype, algo=algo)
+    f = synthetic.wind_fields(nx, ny, nz, 73)
+    phis = synthetic.scalar_fields(nx, ny, nz, 3, 74)
+    U = [m.from_interior(a) for a in f]
+    P = [m.from_interior(a) for a in phis]
+    N = m.step_scalars(*U, P, dt=0.4)
+    X = [t.clone() for t in P]
+    S = m.advect_scalars(*U, X)
+    m.euler(*X, *S, 0.4)  # the Euler update of any three fields, halos refreshed
+    torch.cuda.synchronize()
+    for a, b in zip(N, X):
+        assert torch.equal(a[:, :, :nz], b[:, :, :nz])
+
+
+def test_scalar_step_argument_errors(pw):
+    from paper_2009_12850_b300 import _lib as L
+    m = pw.Mesh(8, 8, 8, 50.0, dtype="f32")
+    U = [m.zeros() for _ in range(3)]
+    P = [m.zeros() for _ in range(2)]
+    with pytest.raises(L.PWError):
+        m.step_scalars(*U, P, [P[0], m.zeros()])          # output aliases an input
+    with pytest.raises(L.PWError):
+        m.step_scalars(*U, P, dt=float("inf"))
     assert m.device_status() == 0
