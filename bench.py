@@ -326,7 +326,9 @@ def run_gpu(args):
            "api": "pw_advect_host (pinned host arrays, x-slabs of %d columns, %d slabs)" % (pipe.slab, pipe.nslab)}
     err = max(float((host_out[q][2:nx + 2, 2:ny + 2, :nz].to(s64[q].device) - s64[q]).abs().max()) for q in range(3))
     e2e["max_abs_diff_vs_device_path"] = err
-    del pipe
+    del pipe, host_in, host_out
+    if want("e2e_theta_5q"):
+        extras["e2e_theta_5q"] = bench_host_scalars(args, world)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -446,6 +448,38 @@ def bench_scalars(args, world, hbm):
                     "hbm_frac": round(bpp * pts / (kms * 1e-3) / 1e9 / hbm, 4)}
         del m, U, P, S
         torch.cuda.empty_cache()
+    return out
+
+
+def bench_host_scalars(args, world):
+    """The paper's hybrid step with theta + 5 q on the device (they travel with
+    the wind, section 3): host arrays of 512 x 512 x 128 FP64 through
+    pw_advect_host_scalars, copies overlapped slab by slab."""
+    import torch
+    from paper_2009_12850_b300 import api
+    nx, ny, nz, n = 512, 512, 128, 6
+    m = api.Mesh(nx, ny, nz, WL.dx, WL.dy, dtype="f64")
+    pipe = api.Pipeline(m)
+    pipe.reserve_scalars(n)
+    wind = synthetic.wind_fields(nx, ny, nz, WL.seed)
+    phis = synthetic.scalar_fields(nx, ny, nz, n, WL.seed + 100)
+    hin = [pipe.empty_host() for _ in range(3 + n)]
+    hout = [pipe.empty_host(out=True) for _ in range(3 + n)]
+    for h, a in zip(hin, list(wind) + list(phis)):
+        h[2:nx + 2, 2:ny + 2, :nz] = torch.from_numpy(a)
+    stream = torch.cuda.current_stream()
+
+    def step(rec):
+        pipe.advect_host(*hin[:3], *hout[:3], scalars=hin[3:], sources=hout[3:], stream=stream)
+    steps = max(3, args.steps // 4)
+    tot, _ = time_steps(step, steps, 2, world)
+    assert m.device_status() == 0
+    moved = (3 + n) * nx * ny * nz * 8 * 2 + (3 * nx * ny * nz * 8 if pipe.nslab > 1 else 0) // nx
+    out = {"workload": f"pw_{nx}x{ny}x{nz}_dx25, wind + theta + 5 q, FP64", "value": world * nx * ny * nz * steps / tot,
+           "unit": UNIT, "ms_per_step": round(tot / steps * 1e3, 3), "bytes_per_step": moved,
+           "GBs": round(moved * steps / tot / 1e9, 1)}
+    del pipe, hin, hout, m
+    torch.cuda.empty_cache()
     return out
 
 
@@ -721,7 +755,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the headline and e2e")
     ap.add_argument("--extras", default=None,
                     help="comma list of extra rows to run (default all): f32, bf16, f64_native, residuals, "
-                         "small_latency, scalars, "
+                         "small_latency, scalars, e2e_theta_5q, "
                          "paper_strong_f32, fused_step, batched, adjoint_loop, precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

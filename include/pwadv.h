@@ -252,8 +252,9 @@ pw_status pw_pipeline_device_fields(const pw_pipeline *p, void **fields6);
 /* The halo fill + PW step of pw_halo_periodic + pw_advect on HOST arrays in the
  * library layout: u, v, w (mesh dtype) in, su, sv, sw (source dtype) out
  * (beta = 1 adds to them, their old values travelling to the device too).
- * Only interior rows of the host arrays are read and written; host halos are
- * neither read nor filled.  Work proceeds in x-slabs: copy-in of slab s,
+ * Only interior points (rows j < ny of columns i < nx, levels k < nz) of the
+ * host arrays are read and written; host halos and padding levels are neither
+ * read nor written.  Work proceeds in x-slabs: copy-in of slab s,
  * device halos, the stencil of slab s-1, copy-out of finished slabs, all on the
  * pipeline's own streams, ordered after the work already queued on `stream`;
  * `stream` then waits for the whole step, and the call returns without
@@ -265,6 +266,21 @@ pw_status pw_pipeline_device_fields(const pw_pipeline *p, void **fields6);
  * must not overlap. */
 pw_status pw_advect_host(pw_pipeline *p, const void *u, const void *v, const void *w, void *su, void *sv,
                          void *sw, int beta, pw_slab_fn on_slab, void *user, void *stream);
+
+/* Device buffers in the pipeline for up to n scalars and their sources (1 <= n
+ * <= PW_MAX_SCALARS; buffers already there are kept).  Synchronises the device. */
+pw_status pw_pipeline_reserve_scalars(pw_pipeline *p, int n);
+
+/* pw_advect_host with n cell-centred scalars advected by the same wind (theta
+ * and q, which the paper's hybrid copies to the device only when the GPU is to
+ * advect them): phi[a] (mesh dtype) and sphi[a] (source dtype) are HOST arrays
+ * in the library layout; they travel, are halo-filled and advected slab by slab
+ * with the wind (pw_advect_scalars), and on_slab follows each slab of all the
+ * sources.  n = 0 is pw_advect_host.  Buffers for n scalars must have been
+ * reserved (pw_pipeline_reserve_scalars). */
+pw_status pw_advect_host_scalars(pw_pipeline *p, const void *u, const void *v, const void *w, void *su,
+                                 void *sv, void *sw, int n, const void *const *phi, void *const *sphi,
+                                 int beta, pw_slab_fn on_slab, void *user, void *stream);
 
 /* Adjoint (transpose of the Jacobian of the map (u,v,w) -> (su,sv,sw) at the
  * given u, v, w) applied to incoming gradients gsu, gsv, gsw, with the periodic

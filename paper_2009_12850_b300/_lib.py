@@ -68,6 +68,9 @@ _SIGS = {
     "pw_pipeline_sync": ([_vp], _i),
     "pw_pipeline_device_fields": ([_vp, ctypes.POINTER(_vp)], _i),
     "pw_advect_host": ([_vp] + [_vp] * 6 + [_i, _vp, _vp, _vp], _i),
+    "pw_pipeline_reserve_scalars": ([_vp, _i], _i),
+    "pw_advect_host_scalars": ([_vp] + [_vp] * 6 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp, _vp,
+                                                       _vp], _i),
     "pw_advect_adjoint": ([_vp] + [_vp] * 9 + [_d, _i, _vp], _i),
     "pw_euler_adjoint": ([_vp] + [_vp] * 9 + [_d, _vp], _i),
     "pw_euler": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
@@ -221,6 +224,16 @@ def pw_advect_host(p, u, v, w, su, sv, sw, beta, on_slab, user, stream):
 def pw_advect_scalars_step(mesh, u, v, w, phi, phin, dt, stream):
     check(_c.pw_advect_scalars_step(mesh, u, v, w, len(phi), _ptrs(phi), _ptrs(phin), float(dt), stream),
           "pw_advect_scalars_step")
+
+
+def pw_pipeline_reserve_scalars(p, n):
+    check(_c.pw_pipeline_reserve_scalars(p, int(n)), "pw_pipeline_reserve_scalars")
+
+
+def pw_advect_host_scalars(p, u, v, w, su, sv, sw, phi, sphi, beta, on_slab, user, stream):
+    fn = ctypes.cast(on_slab, _vp) if on_slab is not None else None
+    check(_c.pw_advect_host_scalars(p, u, v, w, su, sv, sw, len(phi), _ptrs(phi), _ptrs(sphi), int(beta), fn,
+                                    user, stream), "pw_advect_host_scalars")
 
 
 def pw_advect_adjoint(mesh, u, v, w, gsu, gsv, gsw, gu, gv, gw, alpha, beta, stream):

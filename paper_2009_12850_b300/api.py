@@ -305,15 +305,27 @@ class Pipeline:
         m = self.mesh
         return torch.zeros(m.shape, dtype=m.out_dtype if out else m.in_dtype, pin_memory=pin)
 
-    def advect_host(self, u, v, w, su, sv, sw, beta=0, on_slab=None, stream=None):
+    def reserve_scalars(self, n):
+        L.pw_pipeline_reserve_scalars(self.handle, n)
+
+    def advect_host(self, u, v, w, su, sv, sw, beta=0, on_slab=None, stream=None, scalars=None, sources=None):
         """on_slab(i0, i1) runs on a CUDA host thread as each slab of the
-        sources lands in the host arrays (it must not call CUDA)."""
+        sources lands in the host arrays (it must not call CUDA).  scalars /
+        sources: optional lists of host tensors (theta, q and their sources),
+        advected by the same wind in the same step."""
         ins = [self._host(t, n) for t, n in ((u, "u"), (v, "v"), (w, "w"))]
         outs = [self._host(t, n, True) for t, n in ((su, "su"), (sv, "sv"), (sw, "sw"))]
         cb = None
         if on_slab is not None:
             cb = L.SLAB_FN(lambda user, i0, i1: on_slab(i0, i1))
-        L.pw_advect_host(self.handle, *ins, *outs, beta, cb, None, _stream(stream))
+        if scalars:
+            if sources is None or len(sources) != len(scalars):
+                raise ValueError("one host source tensor per scalar")
+            ps = [self._host(t, "phi") for t in scalars]
+            ss = [self._host(t, "sphi", True) for t in sources]
+            L.pw_advect_host_scalars(self.handle, *ins, *outs, ps, ss, beta, cb, None, _stream(stream))
+        else:
+            L.pw_advect_host(self.handle, *ins, *outs, beta, cb, None, _stream(stream))
         self._cb = cb  # kept alive until the next call (which waits for these callbacks)
 
     def sync(self):

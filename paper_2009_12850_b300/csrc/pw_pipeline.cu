@@ -36,6 +36,7 @@ struct pw_pipeline {
     const pw_mesh *mesh;
     int slab, nslab;
     void *dev[6];  // u, v, w, su, sv, sw on the device (library layout)
+    std::vector<void *> sdev;  // scalars then their sources (pw_pipeline_reserve_scalars)
     cudaStream_t s_in, s_c, s_out;
     cudaEvent_t ev_start, ev_last, ev_done;
     std::vector<cudaEvent_t> ev_in, ev_c;
@@ -59,63 +60,91 @@ __global__ void pw_yhalo_kernel(char *f0, char *f1, char *f2, int ny, int64_t co
     for (int q = lane; q < nchunk; q += 32) dst[q] = src[q];
 }
 
-static pw_status pw_yhalo(const pw_pipeline *p, int i_begin, int i_end) {
+// the fields of one host step: device and host base pointers, element size
+struct pw_field_pair {
+    char *dev, *host;
+    size_t es;
+};
+
+// y halos of columns [i_begin, i_end) of the input fields, three per launch
+static pw_status pw_yhalo(const pw_pipeline *p, const std::vector<pw_field_pair> &in, int i_begin, int i_end) {
     const pw_mesh *m = p->mesh;
     const int es = pw_elem_in(m->dtype);
     const int64_t col_stride = (int64_t)m->nzp * es;
     const int nchunk = (int)(((int64_t)m->nz * es + 15) / 16);
     const int64_t work = 4LL * (i_end - i_begin);
     const int warps = 8;
-    dim3 grid((unsigned)((work + warps - 1) / warps), 3);
-    pw_yhalo_kernel<<<grid, warps * 32, 0, p->s_c>>>((char *)p->dev[0], (char *)p->dev[1], (char *)p->dev[2],
-                                                     m->ny, col_stride, nchunk, i_begin, i_end);
-    PW_CUDA(cudaGetLastError());
-    return PW_OK;
-}
-
-// whole column (halo rows included) src -> dst of u, v, w, in halo column indices
-static pw_status pw_copy_column(const pw_pipeline *p, int dst_col, int src_col) {
-    const pw_mesh *m = p->mesh;
-    const size_t es = (size_t)pw_elem_in(m->dtype), col = (size_t)m->si * es;
-    for (int f = 0; f < 3; f++) {
-        char *b = (char *)p->dev[f];
-        PW_CUDA(cudaMemcpyAsync(b + (size_t)dst_col * col, b + (size_t)src_col * col, col,
-                                cudaMemcpyDeviceToDevice, p->s_c));
+    for (size_t f = 0; f < in.size(); f += 3) {
+        const int nf = (int)std::min<size_t>(3, in.size() - f);
+        char *f0 = in[f].dev, *f1 = nf > 1 ? in[f + 1].dev : f0, *f2 = nf > 2 ? in[f + 2].dev : f0;
+        dim3 grid((unsigned)((work + warps - 1) / warps), (unsigned)nf);
+        pw_yhalo_kernel<<<grid, warps * 32, 0, p->s_c>>>(f0, f1, f2, m->ny, col_stride, nchunk, i_begin, i_end);
+        PW_CUDA(cudaGetLastError());
     }
     return PW_OK;
 }
 
-// interior rows of columns [i0, i1) of the fields [f_begin, f_end) between the
-// host arrays and the device copies
-static pw_status pw_copy_rows(const pw_pipeline *p, void *const *host, int f_begin, int f_end, int i0, int i1,
+// whole column (halo rows included) src -> dst of the input fields, in halo column indices
+static pw_status pw_copy_column(const pw_pipeline *p, const std::vector<pw_field_pair> &in, int dst_col,
+                                int src_col) {
+    const size_t col = (size_t)p->mesh->si * (size_t)pw_elem_in(p->mesh->dtype);
+    for (const pw_field_pair &f : in)
+        PW_CUDA(cudaMemcpyAsync(f.dev + (size_t)dst_col * col, f.dev + (size_t)src_col * col, col,
+                                cudaMemcpyDeviceToDevice, p->s_c));
+    return PW_OK;
+}
+
+// interior points (levels k < nz of rows j in [0, ny)) of columns [i0, i1) of the
+// listed fields between host and device: one 2-D copy per field when columns
+// have no padding levels, else a 3-D copy that leaves the padding alone
+static pw_status pw_copy_rows(const pw_pipeline *p, const std::vector<pw_field_pair> &fields, int i0, int i1,
                               bool to_device, cudaStream_t st) {
     if (i1 <= i0) return PW_OK;
     const pw_mesh *m = p->mesh;
-    for (int f = f_begin; f < f_end; f++) {
-        const size_t es = (size_t)(f < 3 ? pw_elem_in(m->dtype) : pw_elem_out(m->dtype));
-        const size_t pitch = (size_t)m->si * es;
-        const size_t off = (size_t)(i0 + 2) * pitch + 2 * (size_t)m->sj * es;
-        const size_t width = (size_t)m->ny * (size_t)m->sj * es;
-        char *d = (char *)p->dev[f] + off;
-        char *h = (char *)host[f] + off;
-        if (to_device)
-            PW_CUDA(cudaMemcpy2DAsync(d, pitch, h, pitch, width, (size_t)(i1 - i0), cudaMemcpyHostToDevice, st));
-        else
-            PW_CUDA(cudaMemcpy2DAsync(h, pitch, d, pitch, width, (size_t)(i1 - i0), cudaMemcpyDeviceToHost, st));
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    for (const pw_field_pair &f : fields) {
+        const size_t pitch = (size_t)m->si * f.es;
+        const size_t off = (size_t)(i0 + 2) * pitch + 2 * (size_t)m->sj * f.es;
+        char *dst = to_device ? f.dev : f.host;
+        char *src = to_device ? f.host : f.dev;
+        if (m->nzp == m->nz) {
+            const size_t width = (size_t)m->ny * (size_t)m->sj * f.es;
+            PW_CUDA(cudaMemcpy2DAsync(dst + off, pitch, src + off, pitch, width, (size_t)(i1 - i0), kind, st));
+        } else {
+            // rows of nz levels, row pitch nzp levels, ny + 4 rows per column
+            cudaMemcpy3DParms c = {};
+            const size_t row = (size_t)m->nzp * f.es;
+            c.srcPtr = make_cudaPitchedPtr(src + off, row, (size_t)m->nz * f.es, (size_t)m->ny + 4);
+            c.dstPtr = make_cudaPitchedPtr(dst + off, row, (size_t)m->nz * f.es, (size_t)m->ny + 4);
+            c.extent = make_cudaExtent((size_t)m->nz * f.es, (size_t)m->ny, (size_t)(i1 - i0));
+            c.kind = kind;
+            PW_CUDA(cudaMemcpy3DAsync(&c, st));
+        }
     }
     return PW_OK;
 }
 
-// the stencil on columns [i0, i1): a view of the mesh that starts at column i0
-static pw_status pw_slab_advect(const pw_pipeline *p, int i0, int i1, int beta) {
+// the stencils on columns [i0, i1): a view of the mesh that starts at column i0
+// (in: u, v, w, scalars; out: su, sv, sw, scalar sources)
+static pw_status pw_slab_advect(const pw_pipeline *p, const std::vector<pw_field_pair> &in,
+                                const std::vector<pw_field_pair> &out, int i0, int i1, int beta) {
     const pw_mesh *m = p->mesh;
     pw_mesh view = *m;
     view.nx = i1 - i0;
     const size_t ei = (size_t)pw_elem_in(m->dtype) * (size_t)m->si * (size_t)i0;
     const size_t eo = (size_t)pw_elem_out(m->dtype) * (size_t)m->si * (size_t)i0;
-    return pw_launch_advect(&view, (char *)p->dev[0] + ei, (char *)p->dev[1] + ei, (char *)p->dev[2] + ei,
-                            (char *)p->dev[3] + eo, (char *)p->dev[4] + eo, (char *)p->dev[5] + eo, beta, p->s_c,
-                            m->tile_j, m->tile_i);
+    pw_status s = pw_launch_advect(&view, in[0].dev + ei, in[1].dev + ei, in[2].dev + ei, out[0].dev + eo,
+                                   out[1].dev + eo, out[2].dev + eo, beta, p->s_c, m->tile_j, m->tile_i);
+    const int n = (int)in.size() - 3;
+    if (s != PW_OK || n == 0) return s;
+    const void *phi[PW_MAX_SCALARS];
+    void *sphi[PW_MAX_SCALARS];
+    for (int a = 0; a < n; a++) {
+        phi[a] = in[3 + a].dev + ei;
+        sphi[a] = out[3 + a].dev + eo;
+    }
+    return pw_launch_advect_scalars(&view, in[0].dev + ei, in[1].dev + ei, in[2].dev + ei, n, phi, sphi, beta,
+                                    p->s_c, m->tile_j, m->tile_i, 0);
 }
 
 static void CUDART_CB pw_slab_note_fn(void *arg) {
@@ -129,6 +158,7 @@ extern "C" void pw_pipeline_destroy(pw_pipeline *p) {
     if (p->s_in) cudaStreamSynchronize(p->s_in);
     if (p->s_out) cudaStreamSynchronize(p->s_out);
     for (int f = 0; f < 6; f++) cudaFree(p->dev[f]);
+    for (void *d : p->sdev) cudaFree(d);
     for (cudaEvent_t e : p->ev_in) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev_c) cudaEventDestroy(e);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
@@ -198,26 +228,59 @@ extern "C" pw_status pw_pipeline_sync(pw_pipeline *p) {
     return PW_OK;
 }
 
-extern "C" pw_status pw_advect_host(pw_pipeline *p, const void *u, const void *v, const void *w, void *su,
-                                    void *sv, void *sw, int beta, pw_slab_fn on_slab, void *user, void *stream) {
+extern "C" pw_status pw_pipeline_reserve_scalars(pw_pipeline *p, int n) {
     if (!p) return pw_fail(PW_ERR_ARG, "pipeline is NULL");
-    if (beta != 0 && beta != 1) return pw_fail(PW_ERR_ARG, "beta must be 0 or 1");
-    void *host[6] = {(void *)u, (void *)v, (void *)w, su, sv, sw};
-    const char *nm[6] = {"u", "v", "w", "su", "sv", "sw"};
-    for (int f = 0; f < 6; f++)
-        if (!host[f]) return pw_fail(PW_ERR_ARG, "host array %s is NULL", nm[f]);
-    for (int a = 0; a < 3; a++)
-        for (int b = 3; b < 6; b++)
-            if (host[a] == host[b]) return pw_fail(PW_ERR_ARG, "%s and %s alias", nm[a], nm[b]);
-    if (su == sv || su == sw || sv == sw) return pw_fail(PW_ERR_ARG, "outputs alias");
+    if (n < 0 || n > PW_MAX_SCALARS) return pw_fail(PW_ERR_ARG, "n = %d scalars (0..%d)", n, PW_MAX_SCALARS);
+    const int have = (int)p->sdev.size() / 2;
+    if (n <= have) return PW_OK;
     const pw_mesh *m = p->mesh;
-    cudaStream_t user_st = (cudaStream_t)stream;
+    PW_CUDA(cudaDeviceSynchronize());  // no step of this pipeline is in flight while buffers change
+    std::vector<void *> fresh(2 * (size_t)n, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 2 * n && e == cudaSuccess; a++) {
+        const bool src = a >= n;
+        const int q = src ? a - n : a;
+        if (q < have) {  // keep the buffers already there
+            fresh[a] = p->sdev[(src ? have : 0) + q];
+            continue;
+        }
+        const size_t bytes = (size_t)m->total * (size_t)(src ? pw_elem_out(m->dtype) : pw_elem_in(m->dtype));
+        e = cudaMalloc(&fresh[a], bytes);
+        if (e == cudaSuccess) e = cudaMemset(fresh[a], 0, bytes);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        for (int a = 0; a < 2 * n; a++) {
+            const bool src = a >= n;
+            const int q = src ? a - n : a;
+            if (q >= have) cudaFree(fresh[a]);
+        }
+        return pw_cuda_fail(e, "pipeline scalar buffers");
+    }
+    p->sdev.swap(fresh);
+    return PW_OK;
+}
+
+// The step on host arrays: the wind and n scalars in, their sources out.
+static pw_status pw_host_step(pw_pipeline *p, const void *const *host_in, void *const *host_out, int n,
+                              int beta, pw_slab_fn on_slab, void *user, cudaStream_t user_st) {
+    const pw_mesh *m = p->mesh;
+    const int have = (int)p->sdev.size() / 2;
+    if (n > have)
+        return pw_fail(PW_ERR_ARG, "%d scalars but buffers for %d reserved (pw_pipeline_reserve_scalars)", n, have);
+    std::vector<pw_field_pair> in, out;
+    const size_t ei = (size_t)pw_elem_in(m->dtype), eo = (size_t)pw_elem_out(m->dtype);
+    for (int f = 0; f < 3 + n; f++) {
+        char *din = (char *)(f < 3 ? p->dev[f] : p->sdev[f - 3]);
+        char *dout = (char *)(f < 3 ? p->dev[3 + f] : p->sdev[have + f - 3]);
+        in.push_back(pw_field_pair{din, (char *)host_in[f], ei});
+        out.push_back(pw_field_pair{dout, (char *)host_out[f], eo});
+    }
     // the notes of the previous call are read by its callbacks: let them finish
     if (p->notes_pending) {
         PW_CUDA(cudaEventSynchronize(p->ev_done));
         p->notes_pending = false;
     }
-    const int nf_in = beta ? 6 : 3;  // with beta = 1 the old sources travel too
     const int last = m->nx - 1;
     const bool precopy = p->nslab > 1;
     pw_status st;
@@ -227,42 +290,43 @@ extern "C" pw_status pw_advect_host(pw_pipeline *p, const void *u, const void *v
     PW_CUDA(cudaStreamWaitEvent(p->s_c, p->ev_start, 0));
     PW_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_start, 0));
 
-    // copy-in: column nx-1 first (the x halo of slab 0), then the slabs in order
+    // copy-in: column nx-1 first (the x halo of slab 0), then the slabs in order;
+    // with beta = 1 the old sources travel too
     if (precopy) {
-        if ((st = pw_copy_rows(p, host, 0, 3, last, last + 1, true, p->s_in)) != PW_OK) return st;
+        if ((st = pw_copy_rows(p, in, last, last + 1, true, p->s_in)) != PW_OK) return st;
         PW_CUDA(cudaEventRecord(p->ev_last, p->s_in));
     }
     for (int s = 0; s < p->nslab; s++) {
         const int i0 = s * p->slab, i1 = std::min(m->nx, i0 + p->slab);
         const int i1w = (precopy && s == p->nslab - 1) ? std::min(i1, last) : i1;  // nx-1 already there
-        if ((st = pw_copy_rows(p, host, 0, 3, i0, i1w, true, p->s_in)) != PW_OK) return st;
-        if (beta && (st = pw_copy_rows(p, host, 3, nf_in, i0, i1, true, p->s_in)) != PW_OK) return st;
+        if ((st = pw_copy_rows(p, in, i0, i1w, true, p->s_in)) != PW_OK) return st;
+        if (beta && (st = pw_copy_rows(p, out, i0, i1, true, p->s_in)) != PW_OK) return st;
         PW_CUDA(cudaEventRecord(p->ev_in[s], p->s_in));
     }
 
-    // compute: halos as the slabs arrive, the stencil one slab behind
+    // compute: halos as the slabs arrive, the stencils one slab behind
     if (precopy) {
         PW_CUDA(cudaStreamWaitEvent(p->s_c, p->ev_last, 0));
-        if ((st = pw_yhalo(p, last, last + 1)) != PW_OK) return st;
-        if ((st = pw_copy_column(p, 1, last + 2)) != PW_OK) return st;  // column -1 <- nx-1
+        if ((st = pw_yhalo(p, in, last, last + 1)) != PW_OK) return st;
+        if ((st = pw_copy_column(p, in, 1, last + 2)) != PW_OK) return st;  // column -1 <- nx-1
     }
     for (int s = 0; s < p->nslab; s++) {
         const int i0 = s * p->slab, i1 = std::min(m->nx, i0 + p->slab);
         PW_CUDA(cudaStreamWaitEvent(p->s_c, p->ev_in[s], 0));
-        if ((st = pw_yhalo(p, i0, i1)) != PW_OK) return st;
+        if ((st = pw_yhalo(p, in, i0, i1)) != PW_OK) return st;
         if (s == 0) {
-            if (!precopy && (st = pw_copy_column(p, 1, last + 2)) != PW_OK) return st;
-            if ((st = pw_copy_column(p, m->nx + 2, 2)) != PW_OK) return st;  // column nx <- 0
+            if (!precopy && (st = pw_copy_column(p, in, 1, last + 2)) != PW_OK) return st;
+            if ((st = pw_copy_column(p, in, m->nx + 2, 2)) != PW_OK) return st;  // column nx <- 0
         }
         if (s >= 1) {
             const int j0 = (s - 1) * p->slab;
-            if ((st = pw_slab_advect(p, j0, i0, beta)) != PW_OK) return st;
+            if ((st = pw_slab_advect(p, in, out, j0, i0, beta)) != PW_OK) return st;
             PW_CUDA(cudaEventRecord(p->ev_c[s - 1], p->s_c));
         }
     }
     {
         const int i0 = (p->nslab - 1) * p->slab;
-        if ((st = pw_slab_advect(p, i0, m->nx, beta)) != PW_OK) return st;
+        if ((st = pw_slab_advect(p, in, out, i0, m->nx, beta)) != PW_OK) return st;
         PW_CUDA(cudaEventRecord(p->ev_c[p->nslab - 1], p->s_c));
     }
 
@@ -270,7 +334,7 @@ extern "C" pw_status pw_advect_host(pw_pipeline *p, const void *u, const void *v
     for (int s = 0; s < p->nslab; s++) {
         const int i0 = s * p->slab, i1 = std::min(m->nx, i0 + p->slab);
         PW_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_c[s], 0));
-        if ((st = pw_copy_rows(p, host, 3, 6, i0, i1, false, p->s_out)) != PW_OK) return st;
+        if ((st = pw_copy_rows(p, out, i0, i1, false, p->s_out)) != PW_OK) return st;
         if (on_slab) {
             p->notes[s] = pw_slab_note{on_slab, user, i0, i1};
             PW_CUDA(cudaLaunchHostFunc(p->s_out, pw_slab_note_fn, &p->notes[s]));
@@ -280,6 +344,50 @@ extern "C" pw_status pw_advect_host(pw_pipeline *p, const void *u, const void *v
     PW_CUDA(cudaStreamWaitEvent(user_st, p->ev_done, 0));
     p->notes_pending = on_slab != nullptr;
     return PW_OK;
+}
+
+// pointers of one call: none NULL, no output aliasing an input or another output
+static pw_status pw_check_host_fields(const void *const *in, void *const *out, int nf) {
+    for (int f = 0; f < nf; f++) {
+        if (!in[f]) return pw_fail(PW_ERR_ARG, "host input %d is NULL", f);
+        if (!out[f]) return pw_fail(PW_ERR_ARG, "host output %d is NULL", f);
+    }
+    for (int a = 0; a < nf; a++)
+        for (int b = 0; b < nf; b++) {
+            if (out[a] == in[b]) return pw_fail(PW_ERR_ARG, "host output %d aliases input %d", a, b);
+            if (b > a && out[a] == out[b]) return pw_fail(PW_ERR_ARG, "host outputs %d and %d alias", a, b);
+        }
+    return PW_OK;
+}
+
+extern "C" pw_status pw_advect_host(pw_pipeline *p, const void *u, const void *v, const void *w, void *su,
+                                    void *sv, void *sw, int beta, pw_slab_fn on_slab, void *user, void *stream) {
+    if (!p) return pw_fail(PW_ERR_ARG, "pipeline is NULL");
+    if (beta != 0 && beta != 1) return pw_fail(PW_ERR_ARG, "beta must be 0 or 1");
+    const void *in[3] = {u, v, w};
+    void *out[3] = {su, sv, sw};
+    pw_status s = pw_check_host_fields(in, out, 3);
+    if (s != PW_OK) return s;
+    return pw_host_step(p, in, out, 0, beta, on_slab, user, (cudaStream_t)stream);
+}
+
+extern "C" pw_status pw_advect_host_scalars(pw_pipeline *p, const void *u, const void *v, const void *w,
+                                            void *su, void *sv, void *sw, int n, const void *const *phi,
+                                            void *const *sphi, int beta, pw_slab_fn on_slab, void *user,
+                                            void *stream) {
+    if (!p) return pw_fail(PW_ERR_ARG, "pipeline is NULL");
+    if (beta != 0 && beta != 1) return pw_fail(PW_ERR_ARG, "beta must be 0 or 1");
+    if (n < 0 || n > PW_MAX_SCALARS) return pw_fail(PW_ERR_ARG, "n = %d scalars (0..%d)", n, PW_MAX_SCALARS);
+    if (n > 0 && (!phi || !sphi)) return pw_fail(PW_ERR_ARG, "scalar pointer arrays are NULL");
+    const void *in[3 + PW_MAX_SCALARS] = {u, v, w};
+    void *out[3 + PW_MAX_SCALARS] = {su, sv, sw};
+    for (int a = 0; a < n; a++) {
+        in[3 + a] = phi[a];
+        out[3 + a] = sphi[a];
+    }
+    pw_status s = pw_check_host_fields(in, out, 3 + n);
+    if (s != PW_OK) return s;
+    return pw_host_step(p, in, out, n, beta, on_slab, user, (cudaStream_t)stream);
 }
 
 extern "C" pw_status pw_pipeline_device_fields(const pw_pipeline *p, void **fields6) {

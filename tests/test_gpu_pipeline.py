@@ -1,6 +1,7 @@
 """GPU tests of the host-memory step (pw_advect_host): results against the FP64
 oracle and bit for bit against the device path (halo fill + stencil), slab
 widths from 1 column to the whole domain, accumulation, host halos left alone,
+scalars (theta, q) travelling with the wind,
 the per-slab callbacks, and reuse of one pipeline over several steps."""
 import threading
 
@@ -159,3 +160,54 @@ def test_pipeline_argument_errors(pw):
         pipe.advect_host(*H, *O, beta=3)
     with pytest.raises(TypeError):
         pipe.advect_host(*H, H[0].double(), O[1], O[2])
+
+
+@pytest.mark.parametrize("dtype,algo", [("f64", "split"), ("f32", "auto"), ("bf16", "auto")])
+@pytest.mark.parametrize("slab", [1, 6, 0, 100])
+def test_host_step_with_scalars(pw, dtype, algo, slab):
+    """theta + q travel with the wind: every source equals the device path's,
+    bit for bit, and host halos of the outputs are left alone."""
+    nx, ny, nz = 31, 19, 14
+    m = pw.Mesh(nx, ny, nz, 45.0, dtype=dtype, algo=algo)
+    pipe = pw.Pipeline(m, slab)
+    pipe.reserve_scalars(3)
+    f = synthetic.wind_fields(nx, ny, nz, 81)
+    phis = synthetic.scalar_fields(nx, ny, nz, 3, 82)
+    H = host_fields(pipe, f)
+    HP = host_fields(pipe, phis)
+    O = [torch.full(m.shape, -3.0, dtype=m.out_dtype).pin_memory() for _ in range(3)]
+    OP = [torch.full(m.shape, -3.0, dtype=m.out_dtype).pin_memory() for _ in range(3)]
+    pipe.advect_host(*H, *O, scalars=HP, sources=OP)
+    pipe.sync()
+    assert m.device_status() == 0
+    U = [m.from_interior(torch.from_numpy(a).to(m.in_dtype)) for a in f]
+    P = [m.from_interior(torch.from_numpy(a).to(m.in_dtype)) for a in phis]
+    S = m.advect(*U)
+    SP = m.advect_scalars(*U, P)
+    torch.cuda.synchronize()
+    mask = torch.ones(m.shape, dtype=torch.bool)
+    mask[2:nx + 2, 2:ny + 2, :nz] = False
+    for o, s in zip(O + OP, list(S) + list(SP)):
+        assert torch.equal(o[2:nx + 2, 2:ny + 2, :nz], m.interior(s).cpu())
+        assert torch.all(o[mask] == -3.0)
+
+
+def test_host_step_scalars_need_reserved_buffers(pw):
+    from paper_2009_12850_b300 import _lib as L
+    m = pw.Mesh(12, 10, 8, 50.0, dtype="f32")
+    pipe = pw.Pipeline(m, 4)
+    H = [pipe.empty_host() for _ in range(3)]
+    O = [pipe.empty_host(out=True) for _ in range(3)]
+    HP = [pipe.empty_host() for _ in range(2)]
+    OP = [pipe.empty_host(out=True) for _ in range(2)]
+    with pytest.raises(L.PWError):
+        pipe.advect_host(*H, *O, scalars=HP, sources=OP)
+    pipe.reserve_scalars(1)
+    with pytest.raises(L.PWError):
+        pipe.advect_host(*H, *O, scalars=HP, sources=OP)
+    pipe.reserve_scalars(2)
+    pipe.advect_host(*H, *O, scalars=HP, sources=OP)
+    with pytest.raises(L.PWError):
+        pipe.advect_host(*H, *O, scalars=HP, sources=[OP[0], O[0]])   # an output listed twice
+    pipe.sync()
+    assert m.device_status() == 0
