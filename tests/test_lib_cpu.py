@@ -63,6 +63,9 @@ def test_null_arguments_rejected(lib):
     assert c.pw_pipeline_slab(z, None, None) == lib.PW_ERR_ARG
     assert c.pw_advect_host(z, *([z] * 6), 0, None, None, z) == lib.PW_ERR_ARG
     assert "pipeline" in lib.last_error()
+    assert c.pw_advect_host_scalars(z, *([z] * 6), 1, arr, arr, 0, None, None, z) == lib.PW_ERR_ARG
+    assert c.pw_pipeline_reserve_scalars(z, 2) == lib.PW_ERR_ARG
+    assert c.pw_advect_scalars_step(z, z, z, z, 1, arr, arr, 0.5, z) == lib.PW_ERR_ARG
     lib.pw_mesh_destroy(z)   # NULL is allowed
     lib.pw_batch_destroy(z)
     lib.pw_pipeline_destroy(z)
