@@ -252,10 +252,12 @@ def run_gpu(args):
     extras = {}
     rows = None if args.extras is None else set(args.extras.split(","))
 
+    # extra rows run on single-GPU runs only: a multi-GPU run measures the
+    # replicated headline step and its e2e
     def want(name):
-        return not args.no_extras and hd == "f64" and (rows is None or name in rows)
+        return not args.no_extras and hd == "f64" and world == 1 and (rows is None or name in rows)
 
-    if not args.no_extras and hd == "f64":
+    if not args.no_extras and hd == "f64" and world == 1:
         for dtype, algo_name in (("f32", "auto"), ("bf16", "auto"), ("f64", "native")):
             key = dtype if algo_name == "auto" else "f64_native"
             if not want(key):
