@@ -54,3 +54,25 @@ def test_reference_arm_rank_gating(monkeypatch, capsys):
         steps, warmup = 1, 3
     bench.run_reference(A())     # non-zero ranks exit without work
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """The reference arm prints one JSON line with the contract's keys (the
+    timed oracle sample is replaced by a fast stand-in here)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "oracle_sample", lambda seconds: (2.0e8, 4, "stand-in sample"))
+
+    class A:
+        steps, warmup = 2, 3
+    bench.run_reference(A())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] == 2.0e8 and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 4
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == bench.WL.name
