@@ -17,6 +17,7 @@ PW_F64, PW_F32, PW_BF16 = 0, 1, 2
 PW_ALGO_AUTO, PW_ALGO_F64_NATIVE, PW_ALGO_F64_SPLIT = 0, 1, 2
 PW_NOALLOC_MAX_NZ = 4096
 PW_MAX_SCALARS = 16
+PW_MAX_NZ = 4096
 
 
 class pw_mesh_desc(ctypes.Structure):

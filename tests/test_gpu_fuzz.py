@@ -91,3 +91,33 @@ def test_random_scalars_and_step(pw, case, dtype, algo):
             r[:, :, -1] = 0.0
         bound = tol(dtype) * 0.3 * cond[q] + ulp * (np.abs(f[q]) + np.abs(r))
         assert np.all(np.abs(got - r) <= bound), q
+
+
+@pytest.mark.parametrize("dtype,algo", KINDS)
+def test_tallest_columns(pw, dtype, algo):
+    """nz = PW_MAX_NZ (4096 levels: many k chunks, the stretched grid down to its
+    finest level): wind and scalar sources against the oracle."""
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz = 6, 5, L.PW_MAX_NZ
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype=dtype, algo=algo)
+    f = rounded(synthetic.wind_fields(nx, ny, nz, 91), dtype)
+    phis = rounded(synthetic.scalar_fields(nx, ny, nz, 2, 92), dtype)
+    U = [m.from_interior(a) for a in f]
+    P = [m.from_interior(a) for a in phis]
+    S = m.advect(*U)
+    SP = m.advect_scalars(*U, P)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    for q in range(3):
+        compare("s" + "uvw"[q], m.interior(S[q]).double().cpu().numpy(), ref[q], cond[q], tol(dtype), tol(dtype))
+    for q, phi in enumerate(phis):
+        r, cd = oracle.advect_scalar(c, *f, phi, want_cond=True)
+        compare(f"scalar{q}", m.interior(SP[q]).double().cpu().numpy(), r, cd, tol(dtype), tol(dtype))
+
+
+def test_too_tall_column_rejected(pw):
+    from paper_2009_12850_b300 import _lib as L
+    with pytest.raises(L.PWError):
+        pw.Mesh(4, 4, L.PW_MAX_NZ + 1, 50.0, dtype="f32")
