@@ -136,10 +136,12 @@ pw_status pw_mesh_device_status(const pw_mesh *mesh, int clear, void *stream, in
  * pw_mesh_device_status(clear = 1) resets it.  Faults nothing; for tests. */
 pw_status pw_selftest_timeout(const pw_mesh *mesh, long long cycles, void *stream);
 
-/* Tile configuration used by the stencil launches of this mesh/* Tile configuration used by the stencil launches of this mesh: rows of columns
- * per CTA (tile_j, 1..32), columns marched per CTA along x (tile_i, >= 1).
- * Set by pw_autotune or by hand; not safe while launches are being enqueued
- * from another thread. */
+/* Tile configuration used by the stencil launches of this mesh: rows of
+ * columns per CTA (tile_j, 1..32; fewer when a CTA would exceed 512 threads for
+ * long columns) and columns marched per CTA along x (tile_i, >= 1; an upper
+ * bound: launches shorten the march, down to 4 columns, while a small domain
+ * would not fill the GPU).  Set by pw_autotune or by hand; not safe while
+ * launches are being enqueued from another thread. */
 pw_status pw_mesh_set_tile(pw_mesh *mesh, int tile_j, int tile_i);
 pw_status pw_mesh_get_tile(const pw_mesh *mesh, int *tile_j, int *tile_i);
 

@@ -32,6 +32,8 @@ __device__ __forceinline__ P2 pk(float a, float b) {
     asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
     return r;
 }
+// the lane of a pair (the other half of the unpack is left unused)
+#pragma nv_diag_suppress 550
 __device__ __forceinline__ float lx(P2 a) {
     float x, y;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
@@ -42,6 +44,7 @@ __device__ __forceinline__ float ly(P2 a) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
     return y;
 }
+#pragma nv_diag_default 550
 __device__ __forceinline__ P2 operator+(P2 a, P2 b) {
     P2 r;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
