@@ -167,6 +167,10 @@ def whole_job_rate(points_per_rank, world, steps, seconds):
     return world * points_per_rank * steps / seconds
 
 
+def world_size():
+    return int(os.environ.get("WORLD_SIZE", "1"))
+
+
 def spin_up(fn, seconds=0.3):
     """Run fn until `seconds` of device work have passed, so that a short timed
     region does not start on a GPU whose clocks dropped while the host was
@@ -304,6 +308,7 @@ def run_gpu(args):
                      ("fused_step", lambda: bench_fused_step(args, world, hbm)),
                      ("batched", lambda: bench_batched(args, world, hbm)),
                      ("adjoint_loop", lambda: bench_adjoint_loop(args)),
+                     ("adjoint_kernel", lambda: bench_adjoint_kernel(args)),
                      ("precision", bench_precision)):
         if want(name):
             extras[name] = fn()
@@ -666,6 +671,42 @@ def bench_adjoint_loop(args):
             "grad_rel_err_f32_vs_f64": {"gu": rel[0], "gv": rel[1], "gw": rel[2]}}
 
 
+def bench_adjoint_kernel(args):
+    """The adjoint stencil alone on the bandwidth workload (1024 x 1024 x 128,
+    FP32): gu, gv, gw = J(u,v,w)^T (gsu, gsv, gsw), 6 fields read and 3 written
+    (36 B/point compulsory)."""
+    import torch
+    from paper_2009_12850_b300 import api
+    wl = WL
+    m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype="f32")
+    U = [m.from_interior(a) for a in synthetic.fields_for(wl)]
+    Y = [m.zeros() for _ in range(3)]
+    for t in Y:
+        t.normal_()
+    G = [m.zeros() for _ in range(3)]
+    stream = torch.cuda.current_stream()
+
+    def step(rec):
+        if rec is None:
+            m.adjoint(*U, *Y, *G, stream=stream)
+            return
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.adjoint(*U, *Y, *G, stream=stream)
+        b.record(stream)
+        rec.append((a, b))
+    steps = max(3, args.steps // 2)
+    _, kms = time_steps(step, steps, 3, world_size())
+    assert m.device_status() == 0
+    pts = wl.points
+    peak = float(load_peaks()[0]["hbm_gbs"])
+    out = {"workload": wl.name, "dtype": "f32", "ms_per_call": round(kms, 4), "value": pts / (kms * 1e-3),
+           "unit": UNIT, "bytes_per_point": 36, "hbm_frac": round(36 * pts / (kms * 1e-3) / 1e9 / peak, 4)}
+    del m, U, Y, G
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_precision():
     """512 x 512 x 160 sheared turbulence: FP32 and BF16 storage against the
     FP64 split path (itself within 1e-12 of the oracle), max and RMS error per
@@ -763,7 +804,7 @@ def main():
     ap.add_argument("--extras", default=None,
                     help="comma list of extra rows to run (default all): f32, bf16, f64_native, residuals, "
                          "small_latency, scalars, e2e_theta_5q, "
-                         "paper_strong_f32, fused_step, batched, adjoint_loop, precision")
+                         "paper_strong_f32, fused_step, batched, adjoint_loop, adjoint_kernel, precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64", help="headline storage type")

@@ -17,7 +17,17 @@
 #include <math.h>
 #include <type_traits>
 
-#include "pw_internal.h"
+#include "pw_march.cuh"  // slab loads with shuffled k edges, vector stores
+
+// two levels per thread for FP32 (twice the threads for the same staged planes)
+template <typename TC>
+struct SlabLoad<float, TC, 2> {
+    static __device__ __forceinline__ void run(const float *p, TC *o) {
+        const float2 a = *reinterpret_cast<const float2 *>(p);
+        o[0] = a.x;
+        o[1] = a.y;
+    }
+};
 
 struct PwAdjGeom {
     int nx, ny, nz, nzp;
@@ -26,16 +36,11 @@ struct PwAdjGeom {
     double tcx, tcy;
 };
 
-template <typename TS, typename TC, int KV>
-__device__ __forceinline__ void pw_adj_col(const TS *row, int kk, TC (&x)[KV + 2]) {
-    // x[0] = level kbase-1 ... x[KV+1] = level kbase+KV (levels past the
-    // logical extent arrived from TMA as 0)
-#pragma unroll
-    for (int m = 0; m < KV + 2; m++) x[m] = pw_to<TC>(row[kk - 1 + m]);
-}
 
+// at most 256 threads, so the six-field gather keeps its values in registers
+// (shared memory limits the CTAs per SM anyway)
 template <typename TS, typename TC, int KV>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(256)
 pw_adjoint_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                  const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap mgu,
                  const __grid_constant__ CUtensorMap mgv, const __grid_constant__ CUtensorMap mgw,
@@ -116,7 +121,6 @@ pw_adjoint_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__
             issue(q - 2 + g.ns);
             issued = q - 1 + g.ns;
         }
-        if (!active) continue;
 
         const int fs = g.field_stride, L = g.kb;
         const TS *Pm = planes + (size_t)((q - 1) % g.ns) * 6 * fs;
@@ -125,7 +129,7 @@ pw_adjoint_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__
         // row offsets: j-1, j, j+1
         const int rS = tj * L, rC = (tj + 1) * L, rN = (tj + 2) * L;
         enum { U = 0, V = 1, W = 2, YU = 3, YV = 4, YW = 5 };
-#define COL(P, F, R, X) pw_adj_col<TS, TC, KV>((P) + (F) * fs + (R), kk, X)
+#define COL(P, F, R, X) pw_col<TS, TC, KV, true, true>((P) + (F) * fs + (R), kk, X)
         using TOut = TS;
         TOut ru[KV], rv[KV], rw[KV];
         {   // ---------------- gu ----------------
@@ -199,14 +203,11 @@ pw_adjoint_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__
             }
         }
 #undef COL
-        const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
-#pragma unroll
-        for (int m = 0; m < KV; m++) {
-            if (m < nvalid) {
-                gu[off + m] = beta ? gu[off + m] + ru[m] : ru[m];
-                gv[off + m] = beta ? gv[off + m] + rv[m] : rv[m];
-                gw[off + m] = beta ? gw[off + m] + rw[m] : rw[m];
-            }
+        if (active) {
+            const long long off = (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + kbase;
+            pw_store<TOut, KV>(gu + off, ru, nvalid, beta);
+            pw_store<TOut, KV>(gv + off, rv, nvalid, beta);
+            pw_store<TOut, KV>(gw + off, rw, nvalid, beta);
         }
     }
 }
@@ -225,8 +226,8 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     int kc_one = (m->nz + unit - 1) / unit * unit;
     g.kc = (kc_one + 2 * g.h <= 256) ? kc_one : 128;
     g.kb = g.kc + 2 * g.h;
-    // rows per CTA: as asked, but no more than 512 threads (long columns)
-    tile_j = tile_j < 512 / (g.kc / KV) ? tile_j : 512 / (g.kc / KV);
+    // rows per CTA: as asked, but no more than 256 threads (long columns)
+    tile_j = tile_j < 256 / (g.kc / KV) ? tile_j : 256 / (g.kc / KV);
     if (tile_j < 1) tile_j = 1;
     g.tj = tile_j;
     tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
@@ -240,7 +241,7 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     g.tcx = m->tcx;
     g.tcy = m->tcy;
     int threads = (g.kc / KV) * tile_j;
-    if (threads > 512) return pw_fail(PW_ERR_SHAPE, "adjoint tile needs %d threads", threads);
+    if (threads > 256) return pw_fail(PW_ERR_SHAPE, "adjoint tile needs %d threads", threads);
     size_t smem = (size_t)ns * 6 * g.field_stride * sizeof(TS) + (size_t)ns * sizeof(uint64_t);
     if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "adjoint tile needs %zu bytes of shared memory", smem);
     CUtensorMap maps[6];
@@ -292,7 +293,7 @@ static pw_status pw_adjoint_common(const pw_mesh *m, const void *u, const void *
     const void *in[6] = {u, v, w, gsu, gsv, gsw};
     void *out[3] = {gu, gv, gw};
     if (m->dtype == PW_F32)
-        return pw_launch_adjoint<float, float, 4>(m, in, out, alpha, beta, add_y, st, 4, m->tile_i, 4);
+        return pw_launch_adjoint<float, float, 2>(m, in, out, alpha, beta, add_y, st, 4, m->tile_i, 4);
     return pw_launch_adjoint<double, double, 2>(m, in, out, alpha, beta, add_y, st, 4, m->tile_i, 4);
 }
 
