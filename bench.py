@@ -388,8 +388,11 @@ def bench_batched(args, world, hbm):
         pts += mb.nx * mb.ny * mb.nz
     b = api.Batch(meshes)
     b.bind(fields, sources)
-    with tf.TemporaryDirectory() as d:
-        tune_ms = b.autotune(os.path.join(d, "tune.txt"))
+    if args.batch_tune:  # a kept cache: a second run reuses the first run's choice
+        tune_ms = b.autotune(args.batch_tune)
+    else:
+        with tf.TemporaryDirectory() as d:
+            tune_ms = b.autotune(os.path.join(d, "tune.txt"))
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -805,6 +808,8 @@ def main():
                     help="comma list of extra rows to run (default all): f32, bf16, f64_native, residuals, "
                          "small_latency, scalars, e2e_theta_5q, "
                          "paper_strong_f32, fused_step, batched, adjoint_loop, adjoint_kernel, precision")
+    ap.add_argument("--batch-tune", default=None,
+                    help="autotuner cache file for the batched row (reused when it exists)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64", help="headline storage type")
