@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -742,12 +743,13 @@ def bench_precision():
 # ----------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline leg and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample(seconds, ncols=64):
+def oracle_sample(seconds, ncols=64, threads=None):
     """Time the FP64 CPU oracle on slabs of the bench workload (ncols x ny x nz
     columns of the same field distribution, periodic) until `seconds` of work
-    have run; returns (points/s, threads, description)."""
+    have run, on `threads` threads (default: every host core); returns
+    (points/s, threads, description)."""
     import oracle
-    threads = oracle.set_threads(os.cpu_count() or 1)
+    threads = oracle.set_threads(threads or os.cpu_count() or 1)
     c = oracle.Coeffs(WL.nz, WL.dx, WL.dy)
     u, v, w = synthetic.wind_fields(ncols, WL.ny, WL.nz, WL.seed)
     oracle.advect(c, u, v, w)  # warm
@@ -762,10 +764,30 @@ def oracle_sample(seconds, ncols=64):
                                f"({done} points, {el:.1f} s)"
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or "unknown"
+
+
 def cpu_baseline(seconds):
     rate, threads, desc = oracle_sample(seconds)
+    rate1, _, desc1 = oracle_sample(min(3.0, seconds / 4), threads=1)
+    oracle_threads_all()
     return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": desc + "; FP64 C oracle, OpenMP over x"}
+            "sample": desc + "; FP64 C oracle, OpenMP over x",
+            "single_thread": {"value": rate1, "unit": UNIT, "sample": desc1},
+            "cpu_model": cpu_model()}
+
+
+def oracle_threads_all():
+    import oracle
+    oracle.set_threads(os.cpu_count() or 1)
 
 
 def run_reference(args):
