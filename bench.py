@@ -36,7 +36,7 @@ from paper_2009_12850_b300 import synthetic  # noqa: E402
 WL = synthetic.LARGE   # replaced by --nx/--ny/--nz for profiling captures of a smaller case
 METRIC = "advected grid points/s (u,v,w) & % HBM roofline; FP32 vs FP64 at stated error"
 UNIT = "points/s"
-BYTES_PER_POINT = {"f64": 48, "f32": 24, "bf16": 18}   # compulsory: read u,v,w + write su,sv,sw
+BYTES_PER_POINT = {"f64": 48, "f32": 24, "bf16": 18, "bf16_out": 12}   # compulsory: read u,v,w + write su,sv,sw
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}
 
 
@@ -268,7 +268,7 @@ def run_gpu(args):
         return not args.no_extras and hd == "f64" and world == 1 and (rows is None or name in rows)
 
     if not args.no_extras and hd == "f64" and world == 1:
-        for dtype, algo_name in (("f32", "auto"), ("bf16", "auto"), ("f64", "native")):
+        for dtype, algo_name in (("f32", "auto"), ("bf16", "auto"), ("bf16_out", "auto"), ("f64", "native")):
             key = dtype if algo_name == "auto" else "f64_native"
             if not want(key):
                 continue
@@ -828,13 +828,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the headline and e2e")
     ap.add_argument("--extras", default=None,
                     help="comma list of extra rows to run (default all): f32, bf16, f64_native, residuals, "
-                         "small_latency, scalars, e2e_theta_5q, "
+                         "bf16_out, small_latency, scalars, e2e_theta_5q, "
                          "paper_strong_f32, fused_step, batched, adjoint_loop, adjoint_kernel, precision")
     ap.add_argument("--batch-tune", default=None,
                     help="autotuner cache file for the batched row (reused when it exists)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64", help="headline storage type")
+    ap.add_argument("--dtype", choices=["f64", "f32", "bf16", "bf16_out"], default="f64", help="headline storage type")
     ap.add_argument("--algo", choices=["auto", "native", "split"], default="auto", help="FP64 arithmetic")
     ap.add_argument("--nx", type=int, default=None, help="smaller domain (ncu captures)")
     ap.add_argument("--ny", type=int, default=None)

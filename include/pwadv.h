@@ -61,7 +61,13 @@ typedef enum {
 typedef enum {
     PW_F64 = 0,   /* u, v, w and su, sv, sw in binary64; result within 1e-12 of FP64 */
     PW_F32 = 1,   /* binary32 storage and FP32 arithmetic */
-    PW_BF16 = 2   /* u, v, w in bfloat16; FP32 arithmetic; su, sv, sw in binary32 */
+    PW_BF16 = 2,  /* u, v, w in bfloat16; FP32 arithmetic; su, sv, sw in binary32 */
+    PW_BF16_OUT = 3 /* u, v, w and su, sv, sw in bfloat16; FP32 arithmetic, each source
+                       rounded once to bfloat16 (12 bytes per point instead of 18): error
+                       within that of PW_BF16 plus 2^-8 |S| (the bfloat16 rounding).
+                       Available for pw_advect, pw_advect_step, the scalar entry points,
+                       pw_residuals, the halo fill and the host pipeline; the adjoint,
+                       Euler and batched entry points return PW_ERR_DTYPE. */
 } pw_dtype;
 
 /* Arithmetic used for PW_F64 meshes (ignored for the other dtypes). */

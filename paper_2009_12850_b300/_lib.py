@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libpwadv.so")
 
 PW_OK, PW_ERR_ARG, PW_ERR_SHAPE, PW_ERR_ALIGN, PW_ERR_DTYPE = 0, -1, -2, -3, -4
 PW_ERR_LID, PW_ERR_CUDA, PW_ERR_TIMEOUT, PW_ERR_NOMEM, PW_ERR_IO = -5, -6, -7, -8, -9
-PW_F64, PW_F32, PW_BF16 = 0, 1, 2
+PW_F64, PW_F32, PW_BF16, PW_BF16_OUT = 0, 1, 2, 3
 PW_ALGO_AUTO, PW_ALGO_F64_NATIVE, PW_ALGO_F64_SPLIT = 0, 1, 2
 PW_NOALLOC_MAX_NZ = 4096
 PW_MAX_SCALARS = 16

@@ -13,10 +13,10 @@ import torch
 
 from . import _lib as L
 
-_DT = {"f64": L.PW_F64, "f32": L.PW_F32, "bf16": L.PW_BF16}
+_DT = {"f64": L.PW_F64, "f32": L.PW_F32, "bf16": L.PW_BF16, "bf16_out": L.PW_BF16_OUT}
 _ALGO = {"auto": L.PW_ALGO_AUTO, "native": L.PW_ALGO_F64_NATIVE, "split": L.PW_ALGO_F64_SPLIT}
-_TORCH_IN = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
-_TORCH_OUT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.float32}
+_TORCH_IN = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16, "bf16_out": torch.bfloat16}
+_TORCH_OUT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.float32, "bf16_out": torch.bfloat16}
 
 
 def _stream(stream=None):

@@ -125,6 +125,9 @@ pw_status pw_launch_advect(const pw_mesh *m, const void *u, const void *v, const
         case PW_BF16:
             return pw_launch_march<__nv_bfloat16, float, float, 4>(m, u, v, w, su, sv, sw, beta, st,
                                                                    tile_j, tile_i, PW_MARCH_NS);
+        case PW_BF16_OUT:
+            return pw_launch_march<__nv_bfloat16, float, __nv_bfloat16, 4>(m, u, v, w, su, sv, sw, beta, st,
+                                                                           tile_j, tile_i, PW_MARCH_NS);
     }
     return pw_fail(PW_ERR_DTYPE, "unknown dtype");
 }
@@ -144,6 +147,7 @@ pw_status pw_launch_step(const pw_mesh *m, const void *u, const void *v, const v
             return pw_launch_march<float, float, float, 4, true>(m, u, v, w, un, vn, wn, 0, st, tile_j, tile_i,
                                                                  PW_MARCH_NS, dt);
         case PW_BF16:
+        case PW_BF16_OUT:  // the new state has the field type either way
             return pw_launch_march<__nv_bfloat16, float, __nv_bfloat16, 4, true>(m, u, v, w, un, vn, wn, 0, st,
                                                                                  tile_j, tile_i, PW_MARCH_NS, dt);
     }

@@ -103,6 +103,22 @@ __device__ __forceinline__ void pw_store(TO *p, const TO (&r)[KV], int nvalid, i
                 for (int m = 0; m < KV; m++) vv[m] = r[m];
             }
             *reinterpret_cast<V *>(p) = val;
+        } else if constexpr (sizeof(TO) * KV == 8) {
+            // four bfloat16 results: one 8-byte store (accumulation in FP32,
+            // rounded once)
+            struct alignas(8) V8 {
+                TO v[KV];
+            };
+            V8 val;
+            if (beta) {
+                const V8 old = *reinterpret_cast<const V8 *>(p);
+#pragma unroll
+                for (int m = 0; m < KV; m++) val.v[m] = (TO)(pw_to<float>(old.v[m]) + pw_to<float>(r[m]));
+            } else {
+#pragma unroll
+                for (int m = 0; m < KV; m++) val.v[m] = r[m];
+            }
+            *reinterpret_cast<V8 *>(p) = val;
         } else {
 #pragma unroll
             for (int m = 0; m < KV; m++) p[m] = beta ? p[m] + r[m] : r[m];

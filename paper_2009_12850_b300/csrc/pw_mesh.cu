@@ -47,7 +47,7 @@ extern "C" const char *pw_status_string(pw_status s) {
 extern "C" int pw_version(void) { return PWADV_VERSION; }
 
 int pw_elem_in(pw_dtype d) { return d == PW_F64 ? 8 : d == PW_F32 ? 4 : 2; }
-int pw_elem_out(pw_dtype d) { return d == PW_F64 ? 8 : 4; }
+int pw_elem_out(pw_dtype d) { return d == PW_F64 ? 8 : d == PW_BF16_OUT ? 2 : 4; }
 
 pw_status pw_check_ptr(const void *p, const char *name) {
     if (!p) return pw_fail(PW_ERR_ARG, "%s is NULL", name);
@@ -204,7 +204,7 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
     if ((int64_t)(d->nx + 4) * (d->ny + 4) > (int64_t)1 << 31 || d->nx > 1 << 20 || d->ny > 1 << 20)
         return pw_fail(PW_ERR_SHAPE, "horizontal size too large");
     if (!(d->dx > 0) || !(d->dy > 0)) return pw_fail(PW_ERR_ARG, "dx and dy must be > 0");
-    if (d->dtype != PW_F64 && d->dtype != PW_F32 && d->dtype != PW_BF16)
+    if (d->dtype != PW_F64 && d->dtype != PW_F32 && d->dtype != PW_BF16 && d->dtype != PW_BF16_OUT)
         return pw_fail(PW_ERR_DTYPE, "unknown dtype %d", (int)d->dtype);
     if (d->algo < PW_ALGO_AUTO || d->algo > PW_ALGO_F64_SPLIT)
         return pw_fail(PW_ERR_ARG, "unknown algo %d", (int)d->algo);
@@ -454,7 +454,8 @@ extern "C" pw_status pw_halo_fold(const pw_mesh *m, void *f1, void *f2, void *f3
         if ((s = pw_check_ptr(f[q], nm[q])) != PW_OK) return s;
         f[n++] = f[q];
     }
-    if (m->dtype == PW_BF16) return pw_fail(PW_ERR_DTYPE, "pw_halo_fold supports PW_F64 and PW_F32 meshes");
+    if (m->dtype != PW_F64 && m->dtype != PW_F32)
+        return pw_fail(PW_ERR_DTYPE, "pw_halo_fold supports PW_F64 and PW_F32 meshes");
     dim3 grid((unsigned)(m->num_sms * 4), (unsigned)n);
     cudaStream_t st = (cudaStream_t)stream;
     void *a = f[0], *b = n > 1 ? f[1] : f[0], *c = n > 2 ? f[2] : f[0];
@@ -574,7 +575,7 @@ pw_residual_pass1(const TF *u, const TF *v, const TF *w, const TS *su, const TS 
         int64_t off = ((int64_t)(i + 2) * (ny + 4) + (j + 2)) * nzp + k;
         double Wc[3] = {wuv[k], wuv[k], ww[k]};
         double f[3] = {pw_to<double>(u[off]), pw_to<double>(v[off]), pw_to<double>(w[off])};
-        double s[3] = {(double)su[off], (double)sv[off], (double)sw[off]};
+        double s[3] = {pw_to<double>(su[off]), pw_to<double>(sv[off]), pw_to<double>(sw[off])};
         if (k == nz - 1) {  // lid face: w and sw are 0 by definition
             f[2] = 0.0;
             s[2] = 0.0;
@@ -628,6 +629,7 @@ pw_status pw_launch_residuals(const pw_mesh *m, const void *u, const void *v, co
         (const TS *)sw, wuv, ww, m->nx, m->ny, m->nz, m->nzp, partials)
     if (m->dtype == PW_F64) PW_RES(double, double);
     else if (m->dtype == PW_F32) PW_RES(float, float);
+    else if (m->dtype == PW_BF16_OUT) PW_RES(__nv_bfloat16, __nv_bfloat16);
     else PW_RES(__nv_bfloat16, float);
 #undef PW_RES
     PW_CUDA(cudaGetLastError());
@@ -648,6 +650,7 @@ pw_status pw_launch_residuals_raw(int nx, int ny, int nz, int nzp, pw_dtype dtyp
         (const TS *)sw, wuv, ww, nx, ny, nz, nzp, partials)
     if (dtype == PW_F64) PW_RES_RAW(double, double);
     else if (dtype == PW_F32) PW_RES_RAW(float, float);
+    else if (dtype == PW_BF16_OUT) PW_RES_RAW(__nv_bfloat16, __nv_bfloat16);
     else PW_RES_RAW(__nv_bfloat16, float);
 #undef PW_RES_RAW
     PW_CUDA(cudaGetLastError());

@@ -309,6 +309,9 @@ pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *
         case PW_BF16:
             return pw_launch_scalars<__nv_bfloat16, float, float, 4>(m, u, v, w, n, phi, sphi, beta, st,
                                                                      tile_j, tile_i, group);
+        case PW_BF16_OUT:
+            return pw_launch_scalars<__nv_bfloat16, float, __nv_bfloat16, 4>(m, u, v, w, n, phi, sphi, beta, st,
+                                                                             tile_j, tile_i, group);
     }
     return pw_fail(PW_ERR_DTYPE, "unknown dtype");
 }
@@ -362,6 +365,7 @@ pw_status pw_launch_scalars_step(const pw_mesh *m, const void *u, const void *v,
             return pw_launch_scalars<float, float, float, 4, true>(m, u, v, w, n, phi, phin, 0, st, tile_j,
                                                                    tile_i, 0, dt);
         case PW_BF16:
+        case PW_BF16_OUT:  // the new state has the field type either way
             return pw_launch_scalars<__nv_bfloat16, float, __nv_bfloat16, 4, true>(m, u, v, w, n, phi, phin, 0,
                                                                                    st, tile_j, tile_i, 0, dt);
     }

@@ -52,7 +52,7 @@ extern "C" pw_status pw_residuals_noalloc(int nx, int ny, int nz, int nzp, pw_dt
         return pw_fail(PW_ERR_SHAPE, "nzp=%d must be >= nz and a multiple of 8", nzp);
     if ((int64_t)(nx + 4) * (ny + 4) > (int64_t)1 << 31)
         return pw_fail(PW_ERR_SHAPE, "horizontal size too large");
-    if (dtype != PW_F64 && dtype != PW_F32 && dtype != PW_BF16)
+    if (dtype != PW_F64 && dtype != PW_F32 && dtype != PW_BF16 && dtype != PW_BF16_OUT)
         return pw_fail(PW_ERR_DTYPE, "unknown dtype %d", (int)dtype);
     if (!w_uv || !w_w || !out) return pw_fail(PW_ERR_ARG, "w_uv, w_w and out must not be NULL");
     const void *ps[6] = {u, v, w, su, sv, sw};
