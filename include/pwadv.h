@@ -181,7 +181,8 @@ pw_status pw_halo_fold(const pw_mesh *mesh, void *f1, void *f2, void *f3, void *
  * (i,j,k).  beta = 0 overwrites su, sv, sw; beta = 1 adds to them (dynamics
  * components add into shared source terms, section 3).  Only interior points
  * k < nz are written.  u, v, w are mesh dtype; su, sv, sw are binary64 for
- * PW_F64 and binary32 otherwise.  Inputs and outputs must not overlap. */
+ * PW_F64, bfloat16 for PW_BF16_OUT and binary32 otherwise.  Inputs and outputs
+ * must not overlap. */
 pw_status pw_advect(const pw_mesh *mesh, const void *u, const void *v, const void *w,
                     void *su, void *sv, void *sw, int beta, void *stream);
 
@@ -213,8 +214,8 @@ pw_status pw_advect_step(const pw_mesh *mesh, const void *u, const void *v, cons
  * tcx, tcy, tzc1, tzc2), w(-1) = 0 at the ground and w(nz-1) = 0 at the lid
  * (never read).  phi and sphi are HOST arrays of n device pointers (1 <= n <=
  * PW_MAX_SCALARS): phi[a] is a field of the mesh dtype and layout with its
- * halos filled (pw_halo_periodic), sphi[a] its source, binary64 for PW_F64 and
- * binary32 otherwise; beta as in pw_advect.  Halos of u, v, w must be filled.
+ * halos filled (pw_halo_periodic), sphi[a] its source, binary64 for PW_F64,
+ * bfloat16 for PW_BF16_OUT and binary32 otherwise; beta as in pw_advect.  Halos of u, v, w must be filled.
  * The wind is read once per group of scalars that fits a CTA's shared memory.
  * FP64 meshes compute in double-float arithmetic on the FP32 pipe (algo
  * PW_ALGO_F64_SPLIT, the default; same accuracy contract as pw_advect) or in
@@ -302,7 +303,7 @@ pw_status pw_advect_host_scalars(pw_pipeline *p, const void *u, const void *v, c
  * (the lid is not a degree of freedom).  Only interior points k < nz of
  * gu, gv, gw are written.  For nz = 1 (sw identically 0) gsw is ignored and
  * overwritten with 0.  FP32 and FP64 meshes (FP64 in native FP64 arithmetic);
- * PW_ERR_DTYPE for BF16.  No argument may alias an output. */
+ * PW_ERR_DTYPE for PW_BF16 and PW_BF16_OUT.  No argument may alias an output. */
 pw_status pw_advect_adjoint(const pw_mesh *mesh, const void *u, const void *v, const void *w,
                             void *gsu, void *gsv, void *gsw,
                             void *gu, void *gv, void *gw, double alpha, int beta, void *stream);
@@ -351,7 +352,8 @@ pw_status pw_residuals(const pw_mesh *mesh, const void *u, const void *v, const 
  * dtype, the energy weights as HOST arrays of nz doubles (w_uv = rho_n dz on
  * u/v levels, w_w = rho_w dzn on w faces with the lid face 0; the last two
  * columns of pw_mesh_coefficients), the DEVICE buffers u, v, w, su, sv, sw
- * (16-byte aligned; sources binary64 for PW_F64, binary32 otherwise) and a HOST
+ * (16-byte aligned; sources binary64 for PW_F64, bfloat16 for PW_BF16_OUT,
+ * binary32 otherwise) and a HOST
  * array out of 12 doubles, filled exactly as by pw_residuals.
  *
  * Allocation: none.  The only scratch is a file-scope device array of about
