@@ -99,3 +99,49 @@ def test_fp64_split_advect_past_2_31_elements(pw):
         assert check_tiled(m, S[q], ref[q], TOL_F64 * cond[q]) <= 1.0, q
     del U, S, m
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_scalars_past_2_31_elements(pw, dtype):
+    torch.cuda.empty_cache()
+    m = pw.Mesh(N, N, NZ, 50.0, dtype=dtype)
+    t = {"f32": torch.float32, "f64": torch.float64}[dtype]
+    rnd = lambda a: torch.from_numpy(a).to(t).double().numpy()   # noqa: E731
+    wind = [rnd(a) for a in synthetic.wind_fields(B, B, NZ, 403)]
+    phis = [rnd(a) for a in synthetic.scalar_fields(B, B, NZ, 1, 404)]
+    U = big_fields(m, wind, t)
+    P = big_fields(m, phis, t)
+    SP = m.advect_scalars(*U, P)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    ref, cond = oracle.advect_scalar(oracle.Coeffs(NZ, 50.0, 50.0), *wind, phis[0], want_cond=True)
+    tol = TOL_F64 if dtype == "f64" else TOL_F32_COND
+    assert check_tiled(m, SP[0], ref, tol * cond) <= 1.0
+    del U, P, SP, m
+    torch.cuda.empty_cache()
+
+
+def test_fp32_adjoint_past_2_31_elements(pw):
+    torch.cuda.empty_cache()
+    m = pw.Mesh(N, N, NZ, 50.0, dtype="f32")
+    rnd = lambda a: torch.from_numpy(a).float().double().numpy()   # noqa: E731
+    wind = [rnd(a) for a in synthetic.wind_fields(B, B, NZ, 405)]
+    rng = np.random.default_rng(406)
+    y = [rnd(rng.standard_normal((B, B, NZ))) for _ in range(3)]
+    y[2][:, :, -1] = 0.0   # sw on the lid has no effect
+    U = big_fields(m, wind, torch.float32)
+    Y = []
+    for a in y:   # the adjoint fills the halo columns of the incoming gradients itself
+        g = torch.from_numpy(a).to(device="cuda", dtype=torch.float32)
+        Y.append(m.from_interior(g.repeat(REP, REP, 1), fill_halo=False))
+        del g
+    G = m.adjoint(*U, *Y)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    c = oracle.Coeffs(NZ, 50.0, 50.0)
+    ref = oracle.adjoint(c, *wind, *y)
+    cond = oracle.adjoint_cond(c, *wind, *y)
+    for q in range(3):
+        assert check_tiled(m, G[q], ref[q], 2 * TOL_F32_COND * cond[q]) <= 1.0, q
+    del U, Y, G, m
+    torch.cuda.empty_cache()
