@@ -113,19 +113,6 @@ __device__ __forceinline__ void split_words(uint32_t xl, uint32_t xh, float &hi,
     lo = tiny ? 0.0f : __uint_as_float(fb) - __uint_as_float(cb);
 }
 
-// Exact float -> double by integer widening (zeros and subnormals -> +-0).
-__device__ __forceinline__ double widen(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t a = b & 0x7fffffffu;
-    uint32_t h = ((a >> 3) + 0x38000000u) | (b & 0x80000000u);
-    uint32_t l = a << 29;
-    if (a < 0x00800000u) {
-        h = b & 0x80000000u;
-        l = 0u;
-    }
-    return __hiloint2double((int)h, (int)l);
-}
-
 // Float -> double by integer widening for normal floats only (no zero or
 // subnormal handling; those come out as a number of magnitude ~2^-127).
 __device__ __forceinline__ double widen_normal(float f) {
