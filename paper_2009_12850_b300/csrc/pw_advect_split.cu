@@ -277,14 +277,15 @@ static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v,
                                  void *su, void *sv, void *sw, int beta, cudaStream_t st,
                                  int tile_j, int tile_i, bool step, double dt) {
     constexpr int NS = 5;
-    // compiled for 4 or 8 rows of columns per CTA (the nearest of the two is used)
+    // compiled for 4 or 8 rows of columns per CTA (the nearest of the two is
+    // used), with 64- or 32-level chunks: 128 threads per CTA either way
     tile_j = tile_j <= 5 ? 4 : 8;
     PwSplitGeom g;
     g.nx = m->nx;
     g.ny = m->ny;
     g.nz = m->nz;
-    const int kc_one = (m->nz + 1) / 2 * 2;
-    g.kc = kc_one <= 64 ? kc_one : 64;
+    const int kc_one = (m->nz + 1) / 2 * 2, kc_max = tile_j == 4 ? 64 : 32;
+    g.kc = kc_one <= kc_max ? kc_one : kc_max;
     g.kb = g.kc + 4;
     tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
     g.tj = tile_j;

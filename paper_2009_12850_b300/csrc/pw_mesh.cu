@@ -244,8 +244,9 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
         pw_mesh_free(m);
         return pw_cuda_fail(e, "device query");
     }
-    // defaults from timing on B300 at 1024 x 1024 x 128 (pw_autotune refines them)
-    m->tile_j = 4;
+    // defaults from timing on B300 at 1024 x 1024 x 128 (pw_autotune refines
+    // them): the double-float kernels run 8 rows x 32-level chunks per CTA
+    m->tile_j = (m->dtype == PW_F64 && m->algo == PW_ALGO_F64_SPLIT) ? 8 : 4;
     m->tile_i = 64;
     double *tmp = nullptr;
     if ((e = cudaMalloc(&m->coef64, 12 * (size_t)nz * sizeof(double))) != cudaSuccess ||

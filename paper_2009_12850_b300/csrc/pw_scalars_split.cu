@@ -243,8 +243,8 @@ pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v
     g.nx = m->nx;
     g.ny = m->ny;
     g.nz = m->nz;
-    const int kc_one = (m->nz + 1) / 2 * 2;
-    g.kc = kc_one <= 64 ? kc_one : 64;
+    const int kc_one = (m->nz + 1) / 2 * 2, kc_max = tile_j == 4 ? 64 : 32;  // 128 threads per CTA
+    g.kc = kc_one <= kc_max ? kc_one : kc_max;
     g.kb = g.kc + 4;
     tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
     g.ti = tile_i;
