@@ -53,7 +53,9 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     const int nt = blockDim.x, tid = threadIdx.x;
     const int nkt = g.kc / 2;
     const int tk = tid % nkt, tj = tid / nkt;
-    const int j0 = blockIdx.x * TJ, i0 = blockIdx.y * g.ti, k0 = blockIdx.z * g.kc;
+    // k chunks are the fastest grid index: the chunks of a column run together,
+    // so the k-halo levels they share are fetched from DRAM once (L2 hits)
+    const int j0 = blockIdx.y * TJ, i0 = blockIdx.z * g.ti, k0 = blockIdx.x * g.kc;
     const int i_end = min(i0 + g.ti, g.nx);
     const int nplanes = i_end - i0 + 2;
     const uint32_t plane_bytes = 3u * (uint32_t)(TJ + 2) * (uint32_t)g.kb * 8u;
@@ -318,9 +320,9 @@ static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v,
                      : tile_j == 4 ? (beta ? pw_advect_split_kernel<NS, 4, true> : pw_advect_split_kernel<NS, 4, false>)
                                    : (beta ? pw_advect_split_kernel<NS, 8, true> : pw_advect_split_kernel<NS, 8, false>);
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
-              (unsigned)((m->nz + g.kc - 1) / g.kc));
-    if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");
+    dim3 grid((unsigned)((m->nz + g.kc - 1) / g.kc), (unsigned)((m->ny + tile_j - 1) / tile_j),
+              (unsigned)((m->nx + tile_i - 1) / tile_i));
+    if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_j or tile_i");
     kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (double *)su, (double *)sv, (double *)sw,
                                       m->coefsplit, g, m->status, (const double *)u, (const double *)v,
                                       (const double *)w, dt);

@@ -49,7 +49,9 @@ pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
                        double dt = 0.0) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (pw_cta_failed(status)) return;
-    const int kchunk = blockIdx.z % g.nkc, grp = blockIdx.z / g.nkc;
+    // k chunks, then scalar groups, are the fastest grid indices: the chunks
+    // and groups of one tile run together and share the wind planes in L2
+    const int kchunk = blockIdx.x % g.nkc, grp = blockIdx.x / g.nkc;
     const int s0 = grp * g.group;
     const int G = min(g.group, g.n - s0);
     const int NF = 3 + G;
@@ -60,7 +62,7 @@ pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     const int nt = blockDim.x, tid = threadIdx.x;
     const int nkt = g.kc / 2;
     const int tk = tid % nkt, tj = tid / nkt;
-    const int j0 = blockIdx.x * TJ, i0 = blockIdx.y * g.ti, k0 = kchunk * g.kc;
+    const int j0 = blockIdx.y * TJ, i0 = blockIdx.z * g.ti, k0 = kchunk * g.kc;
     const int i_end = min(i0 + g.ti, g.nx);
     const int nplanes = i_end - i0 + 2;
     const uint32_t plane_bytes = (uint32_t)NF * (uint32_t)(TJ + 2) * (uint32_t)g.kb * 8u;
@@ -295,9 +297,9 @@ pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v
                                    : (beta ? pw_scalar_split_kernel<NS, 8, true, GM> : pw_scalar_split_kernel<NS, 8, false, GM>);
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long ngroups = (n + group - 1) / group;
-    dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
-              (unsigned)(g.nkc * ngroups));
-    if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");
+    dim3 grid((unsigned)(g.nkc * ngroups), (unsigned)((m->ny + tile_j - 1) / tile_j),
+              (unsigned)((m->nx + tile_i - 1) / tile_i));
+    if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_j or tile_i");
     kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], set, m->coefsplit, g, m->status, dt);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
