@@ -7,8 +7,10 @@
 // stencil runs on the FP32 pipe (packed .f32x2 instructions over two k levels),
 // with FP64 used only for one add per output.
 //
-// Layout of the work: the same x-march as the FP32 kernel.  A CTA owns tile_j
-// rows and a k chunk; TMA brings (j,k) planes of u, v, w (doubles) into a ring
+// Layout of the work: the same x-march as the FP32 kernel.  A CTA of 128 threads
+// owns tile_j rows and a k chunk (8 rows x 32 levels by default, or 4 x 64); the
+// k chunk is the fastest grid index, so the chunks of a column run together and
+// the k-halo levels they share come from L2.  TMA brings (j,k) planes of u, v, w (doubles) into a ring
 // of NS shared-memory slots (levels >= nz and the w lid arrive as zeros: the
 // tensor maps carry the logical k extent); when a plane has landed, all threads
 // convert it in place, 16 bytes at a time, from (x_k, x_k+1) to
