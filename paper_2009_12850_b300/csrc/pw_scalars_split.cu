@@ -262,8 +262,15 @@ pw_status pw_launch_scalars_split(const pw_mesh *m, const void *u, const void *v
     const size_t field_bytes = (size_t)NS * g.field_stride * 8;
     const size_t fixed = 64 + ((size_t)(g.kc / 2) * 3 + 2) * sizeof(float4);
     if (group <= 0) {
+        // the largest group whose CTA still lets 4 CTAs share an SM (228 KB of
+        // shared memory, 1 KB of it reserved per CTA): the double-float arithmetic
+        // needs the warps to hide its latency, so two groups of three scalars at 16
+        // warps per SM beat one group of six at 8 (148 vs 129 G values/s for
+        // theta + 5 q on 1024 x 1024 x 128) although the wind is staged twice
         const long fit = (long)(226 * 1024 - fixed) / (long)field_bytes - 3;
-        group = (int)std::max(1L, std::min((long)std::min(n, PW_SSPLIT_GMAX), fit));
+        const long fit4 = (long)(56 * 1024 - fixed) / (long)field_bytes - 3;
+        const long gmax = std::min((long)std::min(n, PW_SSPLIT_GMAX), fit);
+        group = (int)std::max(1L, fit4 >= 1 ? std::min(gmax, fit4) : gmax);
         const int ngroups = (n + group - 1) / group;
         group = (n + ngroups - 1) / ngroups;
     }
