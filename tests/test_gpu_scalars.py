@@ -82,6 +82,22 @@ def test_scalar_counts_and_groups(pw, n, dtype, algo):
         compare(f"s{q}", got[q], ref, cond, tn, tc)
 
 
+@pytest.mark.parametrize("n", [6, 16])
+@pytest.mark.parametrize("dtype,algo", [("f64", "split"), ("f64", "native"), ("f32", "auto"), ("bf16", "auto")])
+def test_scalar_grouping_does_not_change_results(pw, n, dtype, algo):
+    """Each scalar's source is independent of the group the launch puts it in:
+    n scalars in one call (automatic groups) equal n calls of one scalar, bit
+    for bit, on a tall column (several k chunks) with ragged sizes."""
+    nx, ny, nz = 37, 19, 101
+    m = pw.Mesh(nx, ny, nz, 45.0, dtype=dtype, algo=algo)
+    wind = synthetic.wind_fields(nx, ny, nz, 17)
+    phis = synthetic.scalar_fields(nx, ny, nz, n, 18)
+    together = run_scalars(pw, m, wind, phis)
+    for q, phi in enumerate(phis):
+        alone = run_scalars(pw, m, wind, [phi])[0]
+        assert np.array_equal(together[q], alone), q
+
+
 @pytest.mark.parametrize("tile", [(1, 16), (2, 7), (4, 64), (8, 32), (3, 200)])
 @pytest.mark.parametrize("algo", ["split", "native"])
 def test_scalar_tiles_do_not_change_results(pw, tile, algo):
