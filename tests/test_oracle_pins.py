@@ -473,9 +473,124 @@ def pin_scalar_lid_and_points():
         assert vals[p] == s[i, j, k] and cv[p] == cond[i, j, k]
 
 
+def pin_euler_energy_step():
+    """One forward-Euler step changes each component's energy by exactly
+    dt^2 sum W S^2: sum W (phi + dt S)^2 - sum W phi^2 = 2 dt sum W phi S + dt^2
+    sum W S^2, and the first sum vanishes (energy identity of the PW form)."""
+    rng = np.random.default_rng(25)
+    nx, ny, nz, dt = 6, 5, 7, 7.0
+    c = stretched(nz)
+    x = rand_fields(rng, nx, ny, nz)
+    s = oracle.advect(c, *x)
+    xn = oracle.euler(c, *x, dt, 1)
+    for g in range(3):
+        e0, e1 = wdot(c, x[g], x[g], g), wdot(c, xn[g], xn[g], g)
+        want = dt * dt * wdot(c, s[g], s[g], g)
+        assert want > 1e-3 * e0
+        assert abs((e1 - e0) - want) <= 1e-12 * (e0 + want), (g, e1 - e0, want)
+
+
+def pin_euler_closed_forms():
+    """A 1-D profile carried by a uniform crossing wind: with rho and dz
+    constant the PW sources at the levels away from the ground and the lid
+    reduce to the centred advective derivative, so one Euler step is
+    phi - dt U (phi(+1) - phi(-1)) / (2 h) there, and the carrying components do
+    not change.  Fixes the sign of every component's update and the dt factor."""
+    nx, ny, nz, dx, dy, dz, dt = 7, 6, 6, 40.0, 30.0, 20.0, 3.0
+    U, V = 6.5, -4.25
+    c = oracle.Coeffs(nz, dx, dy, dz=np.full(nz, dz), rho_n=np.ones(nz), rho_w=np.ones(nz), rho0=1.0)
+    i = np.arange(nx)[:, None, None] * np.ones((1, ny, nz))
+    j = np.arange(ny)[None, :, None] * np.ones((nx, 1, nz))
+    prof = lambda n, t: np.sin(2 * np.pi * t / n) + 0.3 * np.cos(4 * np.pi * t / n)
+    inner = slice(1, nz - 2)
+    # v carried along x by u = U (w = 0): every level
+    a = 5.0 + prof(nx, i)
+    u, v, w = np.full((nx, ny, nz), U), a.copy(), np.zeros((nx, ny, nz))
+    xn = oracle.euler(c, u, v, w, dt, 1)
+    want = a - dt * U * (np.roll(a, -1, 0) - np.roll(a, 1, 0)) / (2 * dx)
+    np.testing.assert_allclose(xn[1], want, rtol=0, atol=1e-13 * np.abs(a).max())
+    assert np.array_equal(xn[0], u) and not xn[2].any()
+    # u carried along y by v = V (w = 0): every level
+    b = 3.0 + prof(ny, j)
+    u, v = b.copy(), np.full((nx, ny, nz), V)
+    xn = oracle.euler(c, u, v, w, dt, 1)
+    want = b - dt * V * (np.roll(b, -1, 1) - np.roll(b, 1, 1)) / (2 * dy)
+    np.testing.assert_allclose(xn[0], want, rtol=0, atol=1e-13 * np.abs(b).max())
+    assert np.array_equal(xn[1], v) and not xn[2].any()
+    # w carried along x by u = U, v = V: levels 1 .. nz-3 (the column of w is
+    # uniform there, so its vertical terms cancel)
+    a = 0.4 * prof(nx, i)
+    a[:, :, -1] = 0.0
+    u, v = np.full((nx, ny, nz), U), np.full((nx, ny, nz), V)
+    xn = oracle.euler(c, u, v, a, dt, 1)
+    want = a - dt * U * (np.roll(a, -1, 0) - np.roll(a, 1, 0)) / (2 * dx)
+    np.testing.assert_allclose(xn[2][:, :, inner], want[:, :, inner], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(xn[0][:, :, inner], U, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(xn[1][:, :, inner], V, rtol=0, atol=1e-14)
+
+
+def pin_euler_fixed_point_and_steps():
+    """Uniform horizontal flow is a fixed point of the step (bit for bit), and n
+    steps in one call equal n calls of one step (bit for bit)."""
+    rng = np.random.default_rng(26)
+    nz = 5
+    c = stretched(nz)
+    U = np.full((5, 4, nz), 7.25)
+    V = np.full((5, 4, nz), -3.5)
+    W = np.zeros((5, 4, nz))
+    for a, b in zip(oracle.euler(c, U, V, W, 0.5, 3), (U, V, W)):
+        assert np.array_equal(a, b)
+    x = rand_fields(rng, 5, 6, nz)
+    one = x
+    for _ in range(3):
+        one = oracle.euler(c, *one, 0.5, 1)
+    three = oracle.euler(c, *x, 0.5, 3)
+    for a, b in zip(one, three):
+        assert np.array_equal(a, b)
+    assert not np.array_equal(three[0], x[0])
+
+
+def pin_adjoint_cond():
+    """The gradient's condition sums (every contribution taken in absolute
+    value).  S is homogeneous of degree 2 in (u, v, w), and so is its
+    absolute-value form, so by Euler's theorem
+      sum_P cond_g(P) |x(P)| = 2 sum_m |y(m)| cond_S(m)
+    with cond_S the forward condition sums; the triangle inequality gives
+    |J^T y| <= cond_g pointwise, with equality wherever every contribution to a
+    point has one sign (checked on a one-point y over positive fields)."""
+    rng = np.random.default_rng(27)
+    nx, ny, nz = 6, 7, 6
+    c = stretched(nz)
+    x = rand_fields(rng, nx, ny, nz)
+    x = (x[0] - 5.0, x[1] - 5.0, x[2])           # mixed signs
+    y = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
+    y[2][:, :, -1] = 0.0
+    g = oracle.adjoint(c, *x, *y)
+    cg = oracle.adjoint_cond(c, *x, *y)
+    _, cs = oracle.advect(c, *x, want_cond=True)
+    lhs = sum(float(np.sum(cg[q] * np.abs(x[q]))) for q in range(3))
+    rhs = 2.0 * sum(float(np.sum(np.abs(y[q]) * cs[q])) for q in range(3))
+    assert abs(lhs - rhs) <= 1e-13 * rhs, (lhs, rhs)
+    for q in range(3):
+        assert np.all(np.abs(g[q]) <= cg[q] * (1 + 1e-14))
+    # equality where all contributions share a sign: y = 1 at su(i, j, k) only
+    xp = rand_fields(rng, nx, ny, nz)
+    xp = (np.abs(xp[0]) + 1, np.abs(xp[1]) + 1, np.abs(xp[2]))
+    i, j, k = 3, 3, 2
+    y1 = [np.zeros((nx, ny, nz)) for _ in range(3)]
+    y1[0][i, j, k] = 1.0
+    g1 = oracle.adjoint(c, *xp, *y1)
+    c1 = oracle.adjoint_cond(c, *xp, *y1)
+    for q, p in ((0, (i - 1, j, k)), (0, (i + 1, j, k)), (1, (i, j - 1, k)), (1, (i + 1, j, k))):
+        assert c1[q][p] > 0
+        assert abs(abs(g1[q][p]) - c1[q][p]) <= 1e-15 * c1[q][p], (q, p, g1[q][p], c1[q][p])
+    assert abs(g1[0][i, j, k]) < c1[0][i, j, k] * (1 - 1e-6)      # contributions of both signs
+
+
 PINS = [pin_worked_examples, pin_lid_ignored, pin_coefficients, pin_uniform_flow, pin_energy, pin_skew_adjoint,
         pin_momentum_divergence_free, pin_momentum_identity, pin_continuum_second_order,
         pin_adjoint_dot, pin_adjoint_bruteforce, pin_cond_and_points,
+        pin_euler_energy_step, pin_euler_closed_forms, pin_euler_fixed_point_and_steps, pin_adjoint_cond,
         pin_scalar_worked_examples, pin_scalar_uniform_and_centred, pin_scalar_energy_and_skew,
         pin_scalar_divergence_identity, pin_scalar_continuum_second_order, pin_scalar_lid_and_points]
 
@@ -553,6 +668,20 @@ MUTANTS = {
                               "        double rho_face_below = (k == 0) ? rhon[0] : rhow[k - 1];"),
     "scalar_quarter_width": ("        hz2[k] = 0.5 * rhow[k] / (rhon[k] * dz[k]);",
                              "        hz2[k] = 0.25 * rhow[k] / (rhon[k] * dz[k]);"),
+    "euler_dt_squared": ("            u[m] = u[m] + dt * s[m];",
+                         "            u[m] = u[m] + dt * dt * s[m];"),
+    "euler_v_takes_su": ("            v[m] = v[m] + dt * s[n + m];",
+                         "            v[m] = v[m] + dt * s[m];"),
+    "euler_w_sign": ("            w[m] = w[m] + dt * s[2 * n + m];",
+                     "            w[m] = w[m] - dt * s[2 * n + m];"),
+    "euler_stale_sources": ("        pwo_advect(nx, ny, nz, tcx, tcy, tzc1, tzc2, tzd1, tzd2, u, v, w,\n                   s, s + n",
+                            "        if (t == 0) pwo_advect(nx, ny, nz, tcx, tcy, tzc1, tzc2, tzd1, tzd2, u, v, w,\n                   s, s + n"),
+    "adjoint_cond_signed_face_sum": ("gs[T->src][P] += fabs(sc) * (fabs(a[Q1]) + fabs(a[Q2]));",
+                                     "gs[T->src][P] += fabs(sc * (a[Q1] + a[Q2]));"),
+    "adjoint_cond_wrong_point": ("                        gs[T->a][Q2] += fabs(sc * phi);",
+                                 "                        gs[T->a][Q1] += fabs(sc * phi);"),
+    "adjoint_cond_drops_phi": ("                        gs[T->a][Q1] += fabs(sc * phi);",
+                               "                        gs[T->a][Q1] += fabs(sc);"),
 }
 
 
