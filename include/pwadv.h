@@ -54,7 +54,8 @@ typedef enum {
     PW_ERR_CUDA = -6,     /* a CUDA runtime call failed (text in pw_last_error) */
     PW_ERR_TIMEOUT = -7,  /* a kernel gave up waiting for an asynchronous copy */
     PW_ERR_NOMEM = -8,    /* host or device allocation failed */
-    PW_ERR_IO = -9        /* the autotune cache file could not be read or written */
+    PW_ERR_IO = -9,       /* the autotune cache file could not be read or written */
+    PW_ERR_RANGE = -10    /* a value outside the range of PW_ALGO_F64_SPLIT (see there) */
 } pw_status;
 
 /* Storage type of the fields and sources of a mesh. */
@@ -74,8 +75,26 @@ typedef enum {
 typedef enum {
     PW_ALGO_AUTO = 0,       /* PW_ALGO_F64_SPLIT */
     PW_ALGO_F64_NATIVE = 1, /* FP64 instructions (the DP units of B300 are slow) */
-    PW_ALGO_F64_SPLIT = 2   /* each double split exactly into two floats; products
-                               by FMA-exact FP32 transforms; meets 1e-12 relative */
+    PW_ALGO_F64_SPLIT = 2   /* each double split exactly into two floats (scaled by 2^8),
+                               products by FMA-exact FP32 transforms.  Error at each
+                               point m:  |err| <= 1e-12 cond(m) + 2^-100 B(m) + 2^-140,
+                               cond(m) = sum |c| |phi| (|a1| + |a2|) and B(m) =
+                               sum |c| (|phi| + |a1| + |a2|) over the point's
+                               elementary products c phi (a1 + a2); when every nonzero
+                               input is at least 2^-40 in magnitude the first term
+                               is the bound.  Range: |u|, |v|, |w| below 2^40 (about
+                               1.1e12) and |theta|, |q| of the scalar entry points
+                               below 2^60; a larger value, NaN or Inf is read as 0 and
+                               sets PW_ERR_RANGE in the mesh status word
+                               (pw_mesh_device_status): results that depend on it
+                               carry no guarantee.  Nonzero values below 2^-110 are
+                               read as 0 (within the bound).  The mesh coefficients
+                               must have tcx, tcy, tzc1, tzc2, tzd1, tzd2 in
+                               [2^-16, 2^8] and 0.25 rho_n, 0.25 rho_w in
+                               [2^-36, 2^24] (checked by pw_mesh_create:
+                               PW_ALGO_AUTO then uses native FP64, PW_ALGO_F64_SPLIT
+                               returns PW_ERR_RANGE).  PW_ALGO_F64_NATIVE has none of
+                               these limits. */
 } pw_algo;
 
 typedef struct {
@@ -122,16 +141,23 @@ void pw_mesh_destroy(pw_mesh *mesh);
 pw_status pw_mesh_layout(const pw_mesh *mesh, int64_t *nzp, int64_t *stride_j,
                          int64_t *stride_i, int64_t *total);
 
+/* The arithmetic a PW_F64 mesh uses, with PW_ALGO_AUTO resolved: PW_ALGO_F64_SPLIT,
+ * or PW_ALGO_F64_NATIVE when asked for or when the coefficients are outside the
+ * split range (see pw_algo).  For the other dtypes PW_ALGO_AUTO is returned. */
+pw_status pw_mesh_algo(const pw_mesh *mesh, pw_algo *out);
+
 /* Copy the FP64 vertical grid to host memory `out` (12*nz doubles, in order
  * dz, zf, zn, dzn, rho_n, rho_w, tzc1, tzc2, tzd1, tzd2, W_uv, W_w where
  * W_uv = rho_n dz and W_w = rho_w dzn (0 on the lid face) are the energy
  * weights) and tcx, tcy into out_h[2] (may be NULL).  Synchronous. */
 pw_status pw_mesh_coefficients(const pw_mesh *mesh, double *out, double *out_h);
 
-/* Read (and with clear != 0 reset) the mesh's device status word: 0, or
- * PW_ERR_TIMEOUT when a kernel gave up waiting on an asynchronous copy since the
- * last clear.  The word is sticky: once set, stencil kernels on this mesh
- * return without work until it is cleared.  Synchronises `stream`. */
+/* Read (and with clear != 0 reset) the mesh's device status: 0; PW_ERR_TIMEOUT
+ * when a kernel gave up waiting on an asynchronous copy since the last clear;
+ * else PW_ERR_RANGE when a PW_ALGO_F64_SPLIT kernel met an input outside its
+ * range (see pw_algo).  Both are sticky until cleared; a timeout also makes the
+ * stencil kernels of this mesh return without work until it is cleared (an
+ * out-of-range input does not).  Synchronises `stream`. */
 pw_status pw_mesh_device_status(const pw_mesh *mesh, int clear, void *stream, int *status);
 
 /* Failure-path self-test: launches a kernel that waits, with the library's
@@ -337,6 +363,12 @@ pw_status pw_residuals(const pw_mesh *mesh, const void *u, const void *v, const 
                        const void *su, const void *sv, const void *sw, double *out,
                        void *stream);
 
+/* The six conservation ratios from the twelve sums of pw_residuals (or
+ * pw_residuals_noalloc): out[c] = R_E(c) = sums[4c] / sums[4c+1] and
+ * out[3+c] = R_M(c) = sums[4c+2] / sums[4c+3] for c in (u, v, w), 0 where the
+ * denominator is 0.  Host arrays; pure host arithmetic, no device work. */
+pw_status pw_residual_ratios(const double *sums, double *out);
+
 /* Largest nz accepted by pw_residuals_noalloc. */
 #define PW_NOALLOC_MAX_NZ 4096
 
@@ -358,9 +390,12 @@ pw_status pw_residuals(const pw_mesh *mesh, const void *u, const void *v, const 
  *
  * Allocation: none.  The only scratch is a file-scope device array of about
  * 120 KB, held on every GPU that loads the library until the process exits.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  nz above PW_NOALLOC_MAX_NZ returns PW_ERR_SHAPE.  The
+ * Every call looks up that array's device address (cudaGetSymbolAddress) with
+ * the current device, so it stays right after a context is re-created; the
+ * call synchronises `stream`, so it cannot sit inside a stream capture.  The six
+ * buffers must be device (or managed) memory of the current device: anything
+ * else returns PW_ERR_ARG before any launch.  nz above PW_NOALLOC_MAX_NZ returns
+ * PW_ERR_SHAPE.  The
  * array is shared by every call: each call rewrites all of it that it reads, so
  * nothing depends on earlier contents, but calls that overlap on the GPU (on
  * different streams or host threads) race on it and must be serialised by the

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libpwadv.so")
 
 PW_OK, PW_ERR_ARG, PW_ERR_SHAPE, PW_ERR_ALIGN, PW_ERR_DTYPE = 0, -1, -2, -3, -4
 PW_ERR_LID, PW_ERR_CUDA, PW_ERR_TIMEOUT, PW_ERR_NOMEM, PW_ERR_IO = -5, -6, -7, -8, -9
+PW_ERR_RANGE = -10
 PW_F64, PW_F32, PW_BF16, PW_BF16_OUT = 0, 1, 2, 3
 PW_ALGO_AUTO, PW_ALGO_F64_NATIVE, PW_ALGO_F64_SPLIT = 0, 1, 2
 PW_NOALLOC_MAX_NZ = 4096
@@ -53,6 +54,7 @@ _SIGS = {
     "pw_mesh_destroy": ([_vp], None),
     "pw_mesh_layout": ([_vp, _i64p, _i64p, _i64p, _i64p], _i),
     "pw_mesh_coefficients": ([_vp, _dp, _dp], _i),
+    "pw_mesh_algo": ([_vp, _ip], _i),
     "pw_mesh_device_status": ([_vp, _i, _vp, _ip], _i),
     "pw_mesh_set_tile": ([_vp, _i, _i], _i),
     "pw_selftest_timeout": ([_vp, ctypes.c_longlong, _vp], _i),
@@ -76,6 +78,7 @@ _SIGS = {
     "pw_euler_adjoint": ([_vp] + [_vp] * 9 + [_d, _vp], _i),
     "pw_euler": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
     "pw_residuals": ([_vp] + [_vp] * 6 + [_dp, _vp], _i),
+    "pw_residual_ratios": ([_dp, _dp], _i),
     "pw_check_lid": ([_vp, _vp, _vp], _i),
     "pw_residuals_noalloc": ([_i, _i, _i, _i, _i, _dp, _dp] + [_vp] * 6 + [_dp, _vp], _i),
     "pw_batch_create": ([ctypes.POINTER(_vp), _i, _vp, ctypes.POINTER(_vp)], _i),
@@ -143,6 +146,12 @@ def pw_mesh_coefficients(mesh, nz):
     h = (ctypes.c_double * 2)()
     check(_c.pw_mesh_coefficients(mesh, buf, h), "pw_mesh_coefficients")
     return list(buf), (h[0], h[1])
+
+
+def pw_mesh_algo(mesh):
+    out = ctypes.c_int()
+    check(_c.pw_mesh_algo(mesh, ctypes.byref(out)), "pw_mesh_algo")
+    return out.value
 
 
 def pw_mesh_device_status(mesh, clear, stream):
@@ -257,8 +266,17 @@ def pw_residuals(mesh, u, v, w, su, sv, sw, stream):
     return list(out)
 
 
+def pw_residual_ratios(sums):
+    a = (ctypes.c_double * 12)(*sums)
+    out = (ctypes.c_double * 6)()
+    check(_c.pw_residual_ratios(a, out), "pw_residual_ratios")
+    return list(out)
+
+
 def pw_residuals_noalloc(nx, ny, nz, nzp, dtype, w_uv, w_w, u, v, w, su, sv, sw, stream):
     """Conservation sums with no device allocation (w_uv, w_w: host sequences of nz floats)."""
+    if len(w_uv) != nz or len(w_w) != nz:
+        raise ValueError(f"w_uv and w_w must hold nz={nz} weights each (got {len(w_uv)}, {len(w_w)})")
     a = (ctypes.c_double * nz)(*w_uv)
     b = (ctypes.c_double * nz)(*w_w)
     out = (ctypes.c_double * 12)()

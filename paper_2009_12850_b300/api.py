@@ -193,13 +193,18 @@ class Mesh:
         return np.array(out).reshape(3, 4)
 
     def residuals(self, u, v, w, su, sv, sw, stream=None):
-        s = self.residual_sums(u, v, w, su, sv, sw, stream)
-        re = tuple(s[q, 0] / s[q, 1] if s[q, 1] else 0.0 for q in range(3))
-        rm = tuple(s[q, 2] / s[q, 3] if s[q, 3] else 0.0 for q in range(3))
-        return re, rm
+        """((R_E u, v, w), (R_M u, v, w)) by pw_residual_ratios."""
+        r = L.pw_residual_ratios(list(self.residual_sums(u, v, w, su, sv, sw, stream).reshape(-1)))
+        return tuple(r[:3]), tuple(r[3:])
 
     def check_lid(self, w, stream=None):
         return L.pw_check_lid(self.handle, self._check(w, "w"), _stream(stream)) == L.PW_OK
+
+    @property
+    def algo(self):
+        """The arithmetic this mesh uses: "split" or "native" (FP64), else "auto"."""
+        return {L.PW_ALGO_AUTO: "auto", L.PW_ALGO_F64_NATIVE: "native",
+                L.PW_ALGO_F64_SPLIT: "split"}[L.pw_mesh_algo(self.handle)]
 
     def device_status(self, clear=True, stream=None):
         return L.pw_mesh_device_status(self.handle, clear, _stream(stream))

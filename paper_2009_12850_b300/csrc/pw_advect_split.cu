@@ -102,14 +102,15 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     // 3*(TJ+2) rows (u, v, w); the first 6*(TJ+2) threads also convert one of
     // the two edge chunks (k halo) of a row.
     constexpr int ROWS = 3 * (TJ + 2);
+    bool bad = false;  // a value this thread converted was outside the split range
     auto conv_chunk = [&](double *base, int R, int q) {
         const int f = R / (TJ + 2), r = R - f * (TJ + 2);
         double *cp = base + (size_t)f * fs + (size_t)r * g.kb + 2 * q;
         // (lo, hi) words of two doubles; levels >= nz and the w lid arrived as 0
         const uint4 d = *reinterpret_cast<const uint4 *>(cp);
         float h0, l0, h1, l1;
-        split_words(d.x, d.y, h0, l0);
-        split_words(d.z, d.w, h1, l1);
+        split_words(d.x, d.y, h0, l0, PW_SPLIT_WIND_EHI, bad);
+        split_words(d.z, d.w, h1, l1, PW_SPLIT_WIND_EHI, bad);
         *reinterpret_cast<float4 *>(cp) = make_float4(h0, h1, l0, l1);
     };
     auto convert = [&](int p) {
@@ -275,6 +276,8 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
             sw[off] = BETA ? sw[off] + c0 : c0;
         }
     }
+    // every thread reaches this point (inactive ones only skip the arithmetic)
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(status + PW_STATUS_RANGE_WORD, 1);
 }
 
 static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v, const void *w,

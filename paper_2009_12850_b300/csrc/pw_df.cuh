@@ -96,32 +96,57 @@ __device__ __forceinline__ D2 df_mul(D2 a, D2 b) {
 // ---------------------------------------------------------------------------
 // conversions
 // ---------------------------------------------------------------------------
-// Split a double, given as its two 32-bit words, into (hi, lo): hi = x
-// truncated to 24 significant bits, lo = the next 23 bits (an exact float
-// subtraction removes the implicit bit), so |x - hi - lo| < 2^-46 |x|.
-// Integer operations plus one FP32 subtraction.  Values with |x| < 2^-100
-// (and zeros) give (0, 0); |x| must be below 2^127.
-__device__ __forceinline__ void split_words(uint32_t xl, uint32_t xh, float &hi, float &lo) {
-    // top 23 mantissa bits and the low 8 exponent bits, then rebias 1023 -> 127
-    const uint32_t f = __funnelshift_l(xl, xh, 3) ^ 0x40000000u;
+// Range of the split arithmetic.  Every field value is carried scaled by 2^8
+// (an exact exponent shift taken in the split itself), so every source, being
+// quadratic in the fields, comes out scaled by 2^16 and the join removes it.
+// With the mesh coefficients checked when the mesh is made (tcx, tcy and the
+// vertical coefficients in [2^-16, 2^8], the density factors 0.25 rho in
+// [2^-36, 2^24]) no intermediate product can overflow while the winds stay
+// below 2^40 in magnitude and the scalars, which only meet products with a
+// wind factor, below 2^60.  Larger values, NaN and Inf are read as 0 and
+// reported.  Nonzero values below 2^-110 are read as 0 without a report: the
+// split is exact from there up, and what is lost below is far under the
+// absolute error floor that underflow of the FP32 intermediates sets anyway.
+#define PW_SPLIT_SCALE_LOG2 8
+// biased FP64 exponents, shifted to the exponent field of the high word
+#define PW_SPLIT_ELO (913u << 20)          // 2^-110: smaller values read as 0
+#define PW_SPLIT_WIND_EHI (1063u << 20)    // 2^40: this and above is out of range
+#define PW_SPLIT_SCALAR_EHI (1083u << 20)  // 2^60
+
+// Split a double, given as its two 32-bit words, into (hi, lo) of 2^8 x: hi =
+// 2^8 x truncated to 24 significant bits, lo = the next 23 bits (an exact float
+// subtraction removes the implicit bit), so |2^8 x - hi - lo| < 2^-46 |2^8 x|.
+// Integer operations plus one FP32 subtraction.  A value whose biased exponent
+// lies outside [PW_SPLIT_ELO, ehi) (shifted left by 20) gives (0, 0); one at or
+// above ehi (too large, Inf or NaN) also sets `bad`.
+__device__ __forceinline__ void split_words(uint32_t xl, uint32_t xh, float &hi, float &lo, uint32_t ehi,
+                                            bool &bad) {
+    // top 23 mantissa bits and the low 9 exponent bits; adding 136 << 23 sets
+    // the float exponent field to (e_double - 1023 + 127 + 8) mod 256
+    const uint32_t f = __funnelshift_l(xl, xh, 3) + 0x44000000u;
     const uint32_t hb = (f & 0x7fffffffu) | (xh & 0x80000000u);
     // lo: 1.m x 2^(e-23) minus 2^(e-23), with m the next 23 mantissa bits
     const uint32_t cb = (hb & 0xff800000u) - 0x0b800000u;
     const uint32_t fb = cb | ((xl >> 6) & 0x007fffffu);
-    const bool tiny = (xh & 0x7ff00000u) < 0x39b00000u;  // biased exponent < 923
-    hi = tiny ? 0.0f : __uint_as_float(hb);
-    lo = tiny ? 0.0f : __uint_as_float(fb) - __uint_as_float(cb);
+    const uint32_t e = xh & 0x7ff00000u;
+    const bool inr = (e - PW_SPLIT_ELO) < (ehi - PW_SPLIT_ELO);
+    bad |= e >= ehi;
+    hi = inr ? __uint_as_float(hb) : 0.0f;
+    lo = inr ? __uint_as_float(fb) - __uint_as_float(cb) : 0.0f;
 }
 
-// Float -> double by integer widening for normal floats only (no zero or
-// subnormal handling; those come out as a number of magnitude ~2^-127).
+// 2^-16 f as a double, by integer widening, for normal floats only (no zero or
+// subnormal handling: those come out as a number of magnitude below 2^-142,
+// inside the absolute error floor of the split arithmetic).
 __device__ __forceinline__ double widen_normal(float f) {
     const uint32_t b = __float_as_uint(f);
-    const uint32_t h = (((b & 0x7fffffffu) >> 3) + 0x38000000u) | (b & 0x80000000u);
+    // exponent rebias 127 -> 1023 less the 2^16 scale of the sources
+    const uint32_t h = (((b & 0x7fffffffu) >> 3) + 0x37000000u) | (b & 0x80000000u);
     return __hiloint2double((int)h, (int)(b << 29));
 }
 
-// hi + lo rounded to double with one FP64 add.  Only the exact-zero case needs
+// 2^-16 (hi + lo) rounded to double with one FP64 add: the source held in
+// scaled double-float form, returned unscaled.  Only the exact-zero case needs
 // care: when hi != 0 a zero or subnormal lo is below half an ulp of any result
 // in range, and when hi == 0 a normal lo is widened exactly.
 __device__ __forceinline__ double join(float hi, float lo) {

@@ -24,9 +24,14 @@ struct pw_mesh {
     float *coef32;           // device, 4*nz: tzc1 tzc2 tzd1 tzd2
     float *coefsplit;        // device, 8*(nz+4)+4: float pairs of g, g', r, r' (levels -2..nz+1), tcx, tcy
     double *partials;        // device, residual scratch: (PW_RED_BLOCKS + 1) * 12 doubles
-    int *status;             // device: [0] timeout status (0 or PW_ERR_TIMEOUT), [1] lid flag
+    int *status;             // device: [0] timeout status (0 or PW_ERR_TIMEOUT), [1] lid flag,
+                             // [2] split-range flag, [3] unused
     int tile_j, tile_i;      // stencil tile: rows per CTA, columns marched per CTA
 };
+
+// words of the mesh status array
+#define PW_STATUS_WORDS 4
+#define PW_STATUS_RANGE_WORD 2  // set by the split kernels when a value was outside their range
 
 // reduction geometry of pw_residuals (fixed so the order of sums is fixed)
 #define PW_RED_BLOCKS 592

@@ -40,6 +40,7 @@ extern "C" const char *pw_status_string(pw_status s) {
         case PW_ERR_TIMEOUT: return "device wait timed out";
         case PW_ERR_NOMEM: return "out of memory";
         case PW_ERR_IO: return "autotune cache i/o error";
+        case PW_ERR_RANGE: return "value outside the range of the split FP64 arithmetic";
     }
     return "unknown status";
 }
@@ -253,7 +254,7 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
         (e = cudaMalloc(&m->coef32, 4 * (size_t)nz * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&m->coefsplit, (8 * ((size_t)nz + 4) + 4) * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&m->partials, (PW_RED_BLOCKS + 1) * 12 * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&m->status, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&m->status, PW_STATUS_WORDS * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&tmp, 3 * (size_t)nz * sizeof(double))) != cudaSuccess) {
         pw_mesh_free(m);
         cudaFree(tmp);
@@ -264,7 +265,7 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
         if (d->dz && (e = cudaMemcpyAsync(tmp, d->dz, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if (d->rho_n && (e = cudaMemcpyAsync(tmp + nz, d->rho_n, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if (d->rho_w && (e = cudaMemcpyAsync(tmp + 2 * nz, d->rho_w, nz * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
-        if ((e = cudaMemsetAsync(m->status, 0, 2 * sizeof(int), st)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(m->status, 0, PW_STATUS_WORDS * sizeof(int), st)) != cudaSuccess) break;
         pw_coeffs_kernel<<<1, 256, 0, st>>>(nz, tmp, tmp + nz, tmp + 2 * nz, d->dz != nullptr,
                                            d->rho_n != nullptr, d->rho_w != nullptr, rho0, H,
                                            m->coef64, m->coef32);
@@ -288,6 +289,29 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
     if (e != cudaSuccess) rs = pw_cuda_fail(e, "coefficient read-back");
     for (int q = 0; rs == PW_OK && q < 12 * nz; q++)
         if (!isfinite(h[q])) rs = pw_fail(PW_ERR_ARG, "non-finite vertical coefficient (check dz/rho)");
+    // the split arithmetic needs tcx, tcy and the vertical coefficients in
+    // [2^-16, 2^8] and the density factors 0.25 rho in [2^-36, 2^24] (its
+    // intermediate products then stay inside the FP32 range); PW_ALGO_AUTO falls
+    // back to native FP64 outside that range, PW_ALGO_F64_SPLIT is refused
+    if (rs == PW_OK && m->dtype == PW_F64 && m->algo == PW_ALGO_F64_SPLIT) {
+        const double *rn = h + 4 * nz, *rw = h + 5 * nz, *tz = h + 6 * nz;
+        auto out_of = [](double x, int lo, int hi) { return !(x >= ldexp(1.0, lo) && x <= ldexp(1.0, hi)); };
+        bool bad = out_of(m->tcx, -16, 8) || out_of(m->tcy, -16, 8);
+        for (int k = 0; k < nz && !bad; k++) {
+            bad = out_of(0.25 * rw[k], -36, 24) || out_of(0.25 * rn[k], -36, 24);
+            // tzc1 tzc2 tzd1 tzd2 (tzd 0 on the lid face; tzc1 at k = 0 multiplies
+            // the ground face, w = 0, and is not used)
+            for (int a = (k == 0 ? 1 : 0); a < 4 && !bad; a++)
+                bad = tz[a * nz + k] != 0.0 && out_of(tz[a * nz + k], -16, 8);
+        }
+        if (bad && d->algo == PW_ALGO_F64_SPLIT)
+            rs = pw_fail(PW_ERR_RANGE, "mesh coefficients outside the split range (tcx, tcy, tzc, tzd in "
+                                       "[2^-16, 2^8], 0.25 rho in [2^-36, 2^24]): use PW_ALGO_F64_NATIVE");
+        else if (bad) {
+            m->algo = PW_ALGO_F64_NATIVE;
+            m->tile_j = 4;
+        }
+    }
     free(h);
     if (rs != PW_OK) {
         pw_mesh_free(m);
@@ -309,6 +333,12 @@ extern "C" pw_status pw_mesh_layout(const pw_mesh *m, int64_t *nzp, int64_t *sj,
     return PW_OK;
 }
 
+extern "C" pw_status pw_mesh_algo(const pw_mesh *m, pw_algo *out) {
+    if (!m || !out) return pw_fail(PW_ERR_ARG, "mesh and out must not be NULL");
+    *out = m->dtype == PW_F64 ? m->algo : PW_ALGO_AUTO;
+    return PW_OK;
+}
+
 extern "C" pw_status pw_mesh_coefficients(const pw_mesh *m, double *out, double *out_h) {
     if (!m || !out) return pw_fail(PW_ERR_ARG, "mesh and out must not be NULL");
     PW_CUDA(cudaMemcpy(out, m->coef64, 12 * (size_t)m->nz * sizeof(double), cudaMemcpyDeviceToHost));
@@ -322,11 +352,14 @@ extern "C" pw_status pw_mesh_coefficients(const pw_mesh *m, double *out, double 
 extern "C" pw_status pw_mesh_device_status(const pw_mesh *m, int clear, void *stream, int *status) {
     if (!m || !status) return pw_fail(PW_ERR_ARG, "mesh and status must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    int h = 0;
-    PW_CUDA(cudaMemcpyAsync(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (clear) PW_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), st));
+    int h[PW_STATUS_WORDS] = {0};
+    PW_CUDA(cudaMemcpyAsync(h, m->status, sizeof(h), cudaMemcpyDeviceToHost, st));
+    if (clear) {
+        PW_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), st));
+        PW_CUDA(cudaMemsetAsync(m->status + PW_STATUS_RANGE_WORD, 0, sizeof(int), st));
+    }
     PW_CUDA(cudaStreamSynchronize(st));
-    *status = h;
+    *status = h[0] != 0 ? h[0] : h[PW_STATUS_RANGE_WORD] != 0 ? (int)PW_ERR_RANGE : 0;
     return PW_OK;
 }
 
@@ -676,6 +709,15 @@ extern "C" pw_status pw_residuals(const pw_mesh *m, const void *u, const void *v
         return s;
     PW_CUDA(cudaMemcpyAsync(out, final_sums, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
     PW_CUDA(cudaStreamSynchronize(st));
+    return PW_OK;
+}
+
+extern "C" pw_status pw_residual_ratios(const double *sums, double *out) {
+    if (!sums || !out) return pw_fail(PW_ERR_ARG, "sums and out must not be NULL");
+    for (int c = 0; c < 3; c++) {
+        out[c] = sums[4 * c + 1] != 0.0 ? sums[4 * c] / sums[4 * c + 1] : 0.0;
+        out[3 + c] = sums[4 * c + 3] != 0.0 ? sums[4 * c + 2] / sums[4 * c + 3] : 0.0;
+    }
     return PW_OK;
 }
 

@@ -107,13 +107,16 @@ pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     // chunk tk+1 of rows tj, tj+TJ, ...; the k-halo chunks 0 and nkt+1 of every
     // row are shared out over all threads
     const int rows = NF * (TJ + 2);
+    bool bad = false;  // a value this thread converted was outside the split range
     auto conv_chunk = [&](double *base, int R, int c) {
         const int f = R / (TJ + 2), r = R - f * (TJ + 2);
         double *cp = base + (size_t)f * fs + (size_t)r * g.kb + 2 * c;
         const uint4 d = *reinterpret_cast<const uint4 *>(cp);
+        // the winds (planes 0..2) and the scalars have their own ranges
+        const uint32_t ehi = f < 3 ? PW_SPLIT_WIND_EHI : PW_SPLIT_SCALAR_EHI;
         float h0, l0, h1, l1;
-        split_words(d.x, d.y, h0, l0);
-        split_words(d.z, d.w, h1, l1);
+        split_words(d.x, d.y, h0, l0, ehi, bad);
+        split_words(d.z, d.w, h1, l1, ehi, bad);
         *reinterpret_cast<float4 *>(cp) = make_float4(h0, h1, l0, l1);
     };
     auto convert = [&](int p) {
@@ -230,7 +233,7 @@ pw_scalar_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
         }
         uM = uC;
     }
-    __syncthreads();
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(status + PW_STATUS_RANGE_WORD, 1);
     if (tid == 0)
         for (int s = 0; s < NS; s++) pw_mbar_inval(&bars[s]);
 }

@@ -8,8 +8,6 @@
 // creating one allocates.  pw_residuals_noalloc serves them: the caller passes
 // the field/source buffers, the layout and the energy weights (host arrays),
 // and the library uses a file-scope device array as its only scratch.
-#include <mutex>
-
 #include "pw_internal.h"
 
 // Scratch: PW_RED_BLOCKS*12 block partials, 12 final sums, then the two weight
@@ -17,25 +15,34 @@
 // holds this array (about 120 KB) until the process exits.
 static __device__ __align__(256) double pw_noalloc_scratch[(PW_RED_BLOCKS + 1) * 12 + 2 * PW_NOALLOC_MAX_NZ];
 
-static std::mutex g_noalloc_mu;
-static double *g_noalloc_addr[256];  // device address of the array, per device ordinal
-
 // Device address of the scratch array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, called once per device with that device current.
+// cudaGetSymbolAddress, with the device current.  It is looked up on every call
+// (a cheap host query; the call synchronises its stream anyway): a context
+// re-created after cudaDeviceReset may place the array elsewhere, so a cached
+// address could go stale.
 static pw_status pw_noalloc_scratch_ptr(double **out) {
-    int dev = 0;
-    PW_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return pw_fail(PW_ERR_ARG, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, pw_noalloc_scratch);
-        if (e != cudaSuccess) return pw_cuda_fail(e, "cudaGetSymbolAddress(pw_noalloc_scratch)");
-        if (!p) return pw_fail(PW_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
-        g_noalloc_addr[dev] = (double *)p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, pw_noalloc_scratch);
+    if (e != cudaSuccess) return pw_cuda_fail(e, "cudaGetSymbolAddress(pw_noalloc_scratch)");
+    if (!p) return pw_fail(PW_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+    *out = (double *)p;
+    return PW_OK;
+}
+
+// The fields must be device (or managed) memory of the current device: a host
+// pointer or another GPU's buffer would otherwise reach the kernel and fault.
+static pw_status pw_check_device_ptr(const void *p, const char *name, int dev) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return pw_fail(PW_ERR_ARG, "%s is not a CUDA allocation", name);
     }
-    *out = g_noalloc_addr[dev];
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return pw_fail(PW_ERR_ARG, "%s is not device memory (memory type %d)", name, (int)a.type);
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return pw_fail(PW_ERR_ARG, "%s lives on device %d, the current device is %d", name, a.device, dev);
     return PW_OK;
 }
 
@@ -57,8 +64,11 @@ extern "C" pw_status pw_residuals_noalloc(int nx, int ny, int nz, int nzp, pw_dt
     if (!w_uv || !w_w || !out) return pw_fail(PW_ERR_ARG, "w_uv, w_w and out must not be NULL");
     const void *ps[6] = {u, v, w, su, sv, sw};
     const char *nm[6] = {"u", "v", "w", "su", "sv", "sw"};
+    int dev = 0;
+    PW_CUDA(cudaGetDevice(&dev));
     for (int q = 0; q < 6; q++) {
         pw_status s = pw_check_ptr(ps[q], nm[q]);
+        if (s == PW_OK) s = pw_check_device_ptr(ps[q], nm[q], dev);
         if (s != PW_OK) return s;
     }
     double *scratch = nullptr;

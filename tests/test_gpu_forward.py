@@ -246,21 +246,173 @@ def test_tiles_do_not_change_results(pw, tile):
         assert np.array_equal(a[q], b[q])
 
 
-@pytest.mark.parametrize("scale", [1e-6, 1e-3, 1.0, 1e3, 1e9])
-def test_split_magnitude_range(pw, scale):
-    """The split path keeps 1e-12 of the condition sum for field magnitudes
-    across its documented range, with mixed signs and exact zeros."""
+# the split arithmetic: inputs below 2^40 in magnitude; the 1e-12 condition
+# bound alone holds when every nonzero value is at least 2^-40, and in general
+# |err| <= 1e-12 cond + 2^-100 B + 2^-140 with B = sum |c| (|phi| + |a1| + |a2|)
+SPLIT_LO, SPLIT_HI = 2.0 ** -40, 2.0 ** 40
+FLOOR_ABS = 2.0 ** -140
+
+
+def _log_uniform(rng, lo, hi, shape, zeros=0.1):
+    """Random signs and magnitudes spread evenly in log2 over [lo, hi), with a
+    fraction of exact zeros."""
+    x = np.exp2(rng.uniform(np.log2(lo), np.log2(hi), shape)) * rng.choice([-1.0, 1.0], shape)
+    x = np.minimum(np.abs(x), np.nextafter(hi, 0)) * np.sign(x)
+    x[rng.random(shape) < zeros] = 0.0
+    return x
+
+
+def local_max(fields):
+    """Largest |value| of any field over the 3x3x3 neighbourhood of each point
+    (periodic in x and y; every operand of a point's stencil lies in it)."""
+    a = np.maximum.reduce([np.abs(f) for f in fields])
+    for ax in (0, 1):
+        a = np.maximum.reduce([a, np.roll(a, 1, ax), np.roll(a, -1, ax)])
+    up = np.concatenate([a[:, :, 1:], a[:, :, -1:]], axis=2)
+    dn = np.concatenate([a[:, :, :1], a[:, :, :-1]], axis=2)
+    return np.maximum.reduce([a, up, dn])
+
+
+def check_split_bound(name, got, ref, cond, floor):
+    err = np.abs(got - ref)
+    bad = err > 1e-12 * cond + floor
+    assert not bad.any(), (f"{name}: {int(bad.sum())} points above 1e-12 cond + floor; worst excess "
+                           f"{float((err - 1e-12 * cond - floor).max()):.3e}")
+
+
+@pytest.mark.parametrize("lo,hi", [(2.0 ** -40, 2.0 ** -36), (1e-6, 1e-5), (1.0, 10.0), (1e9, 1e10),
+                                   (2.0 ** 36, 2.0 ** 40), (2.0 ** -40, 2.0 ** 40), (2.0 ** -12, 2.0 ** 12)],
+                         ids=lambda x: f"{x:.3g}")
+def test_split_magnitude_range(pw, lo, hi):
+    """The split path keeps 1e-12 of each point's condition sum (2^-140 of
+    absolute slack) for values across [2^-40, 2^40) -- at both ends, and with
+    magnitudes mixed over the whole range inside one stencil -- with mixed signs
+    and exact zeros, and reports nothing."""
     nx, ny, nz = 24, 20, 18
     m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo="split")
     rng = np.random.default_rng(21)
-    f = [scale * rng.standard_normal((nx, ny, nz)) * np.exp(rng.uniform(-3, 3, (nx, ny, nz))) for _ in range(3)]
-    f[0][::3, ::2, ::5] = 0.0
+    f = [_log_uniform(rng, lo, hi, (nx, ny, nz)) for _ in range(3)]
     f[2][:, :, -1] = 0.0
     c = oracle.Coeffs(nz, 50.0, 50.0)
     ref, cond = oracle.advect(c, *f, want_cond=True)
     got, _, _ = run_forward(pw, m, f)
     for q in range(3):
-        compare(f"split x{scale:g} s{'uvw'[q]}", got[q], ref[q], cond[q], TOL_F64, TOL_F64)
+        check_split_bound(f"split [{lo:g}, {hi:g}) s{'uvw'[q]}", got[q], ref[q], cond[q], FLOOR_ABS)
+    assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("lo,hi", [(2.0 ** -130, 2.0 ** -100), (2.0 ** -110, 2.0 ** -60), (2.0 ** -90, 2.0 ** -40),
+                                   (2.0 ** -130, 2.0 ** 39)], ids=lambda x: f"{x:.3g}")
+def test_split_small_values(pw, lo, hi):
+    """Values below 2^-40 (down to and past the 2^-110 read-as-zero limit,
+    alone and mixed with large ones): within 1e-12 cond + 2^-100 B + 2^-140,
+    B bounded by 1.5 x (largest |value| around the point) x (the condition sum
+    of all-ones fields); nothing is reported."""
+    nx, ny, nz = 22, 19, 15
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo="split")
+    rng = np.random.default_rng(23)
+    f = [_log_uniform(rng, lo, hi, (nx, ny, nz)) for _ in range(3)]
+    f[2][:, :, -1] = 0.0
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    _, q1 = oracle.advect(c, *[np.ones((nx, ny, nz))] * 3, want_cond=True)
+    vloc = local_max(f)
+    got, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        floor = 2.0 ** -100 * 1.5 * vloc * q1[q] + FLOOR_ABS
+        check_split_bound(f"split small [{lo:g}, {hi:g}) s{'uvw'[q]}", got[q], ref[q], cond[q], floor)
+    assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("corner", ["small", "large"])
+def test_split_coefficient_corners(pw, corner):
+    """Mesh coefficients at the ends of the accepted ranges (tcx, tcy, tzc,
+    tzd in [2^-16, 2^8], 0.25 rho in [2^-36, 2^24]) with values at the matching
+    ends of theirs: the smallest values with the smallest coefficients and
+    density (the products nearest underflow) and the largest with the largest
+    (nearest overflow)."""
+    nx, ny, nz = 20, 17, 12
+    if corner == "small":
+        # 0.25 rho = 2^-36; tzc = 0.25 rho_w / (rho_n dz) = 0.25 / dz = 2^-16; tcx = 2^-16
+        rho, dz, dx = np.full(nz, 2.0 ** -34), np.full(nz, 2.0 ** 14), 0.25 * 2.0 ** 16
+        vlo, vhi = SPLIT_LO, 2.0 ** -36
+    else:
+        # 0.25 rho = 2^24; tzc = 0.25 / dz = 2^8; tcx = 2^8
+        rho, dz, dx = np.full(nz, 2.0 ** 26), np.full(nz, 2.0 ** -10), 0.25 * 2.0 ** -8
+        vlo, vhi = 2.0 ** 36, SPLIT_HI
+    m = pw.Mesh(nx, ny, nz, dx, dz=dz, rho_n=rho, rho_w=rho, rho0=rho[0], H=1.0, dtype="f64", algo="split")
+    assert m.algo == "split"
+    rng = np.random.default_rng(22)
+    f = [_log_uniform(rng, vlo, vhi, (nx, ny, nz), zeros=0.05) for _ in range(3)]
+    f[2][:, :, -1] = 0.0
+    c = oracle.Coeffs(nz, dx, dx, dz=dz, rho_n=rho, rho_w=rho, rho0=rho[0], H=1.0)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    got, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        check_split_bound(f"split {corner} corner s{'uvw'[q]}", got[q], ref[q], cond[q], FLOOR_ABS)
+    assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("bad", ["huge", "nan", "inf"])
+@pytest.mark.parametrize("field", [0, 1, 2])
+def test_split_out_of_range_is_reported(pw, bad, field):
+    """An input at or above 2^40 in magnitude, NaN or Inf sets PW_ERR_RANGE in
+    the mesh status (sticky until cleared; the next clean call reports 0); every
+    point whose stencil does not touch the value still meets the bound.  Tiny
+    values and subnormal doubles read as 0 without a report."""
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz = 19, 16, 14
+    m, f = make(pw, nx, ny, nz, algo="split")
+    value = {"huge": -(2.0 ** 40), "nan": np.nan, "inf": np.inf}[bad]
+    i, j, k = 9, 7, 5
+    g = [a.copy() for a in f]
+    g[field][i, j, k] = value
+    U = [m.from_interior(a) for a in g]
+    S = m.advect(*U)
+    torch.cuda.synchronize()
+    assert m.device_status(clear=False) == L.PW_ERR_RANGE
+    assert m.device_status() == L.PW_ERR_RANGE      # read and clear
+    assert m.device_status() == 0
+    # points more than one cell from (i, j, k) in x or y do not see the value
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    far = np.ones((nx, ny, nz), bool)
+    far[i - 2:i + 3, j - 2:j + 3, :] = False
+    for q in range(3):
+        out = m.interior(S[q]).double().cpu().numpy()
+        compare("far points", out[far], ref[q][far], cond[q][far], TOL_F64, TOL_F64)
+    # the same fields in range give no report
+    m.advect(*[m.from_interior(a) for a in f])
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    # values below 2^-110 and subnormal doubles read as 0, without a report
+    for tiny in (2.0 ** -111, 5e-324):
+        g = [a.copy() for a in f]
+        g[field][i, j, k] = tiny
+        m.advect(*[m.from_interior(a) for a in g])
+        torch.cuda.synchronize()
+        assert m.device_status() == 0
+
+
+def test_coefficients_outside_split_range(pw):
+    """A mesh whose coefficients leave [2^-16, 2^8] (here tcx = 0.25/dx with
+    dx = 10 km... 2.5e-6 < 2^-16) is refused for the split arithmetic and runs
+    native FP64 under auto, still within 1e-12 of the oracle."""
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz, dx = 12, 10, 9, 1.0e5
+    with pytest.raises(L.PWError) as e:
+        pw.Mesh(nx, ny, nz, dx, dtype="f64", algo="split")
+    assert e.value.status == L.PW_ERR_RANGE
+    m = pw.Mesh(nx, ny, nz, dx, dtype="f64", algo="auto")
+    assert m.algo == "native"
+    assert pw.Mesh(nx, ny, nz, 50.0, dtype="f64").algo == "split"
+    assert pw.Mesh(nx, ny, nz, dx, dtype="f32").algo == "auto"
+    f = synthetic.wind_fields(nx, ny, nz, 4)
+    c = oracle.Coeffs(nz, dx, dx)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    got, _, _ = run_forward(pw, m, f)
+    for q in range(3):
+        compare("auto -> native", got[q], ref[q], cond[q], TOL_F64, TOL_F64)
 
 
 @pytest.mark.parametrize("tile", [(1, 1), (3, 5), (8, 7), (4, 1000), (2, 64)])

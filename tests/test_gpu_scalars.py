@@ -211,16 +211,65 @@ def test_scalars_full_size_sampled(pw, dtype, algo):
         compare(f"s{q}", got, ref, cond, tn, tc)
 
 
-@pytest.mark.parametrize("scale", [1e-6, 1e3, 1e9])
-def test_split_scalars_magnitude_range(pw, scale):
-    """The double-float path keeps 1e-12 of the condition sum across magnitudes,
-    with mixed signs and exact zeros in the scalar."""
+def _log_uniform(rng, lo, hi, shape, zeros=0.1):
+    x = np.exp2(rng.uniform(np.log2(lo), np.log2(hi), shape)) * rng.choice([-1.0, 1.0], shape)
+    x = np.minimum(np.abs(x), np.nextafter(hi, 0)) * np.sign(x)
+    x[rng.random(shape) < zeros] = 0.0
+    return x
+
+
+@pytest.mark.parametrize("lo,hi,wide_wind", [(2.0 ** -60, 2.0 ** -56, False), (1e-17, 1e-15, False),
+                                             (1e-6, 1e3, False), (2.0 ** 56, 2.0 ** 60, False),
+                                             (2.0 ** -110, 2.0 ** 60, False), (2.0 ** -60, 2.0 ** 60, True)],
+                         ids=lambda x: f"{x:.3g}" if isinstance(x, float) else str(x))
+def test_split_scalars_magnitude_range(pw, lo, hi, wide_wind):
+    """The double-float path keeps the split bound for scalars across their
+    range (below 2^60; moisture fields far below 1e-12 kg/kg included), with
+    mixed signs and exact zeros, also under winds spread over [2^-40, 2^40):
+    |err| <= 1e-12 cond + 2^-100 B + 2^-140, B = sum |h| (|wind| + |phi|) <=
+    2 (largest |value| around the point) x (the condition sum of all-ones
+    fields); nothing is reported."""
     nx, ny, nz = 23, 19, 33
     m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo="split")
-    wind = synthetic.wind_fields(nx, ny, nz, 25)
     rng = np.random.default_rng(26)
-    phi = scale * rng.standard_normal((nx, ny, nz))
-    phi[rng.random((nx, ny, nz)) < 0.1] = 0.0
+    if wide_wind:
+        wind = [_log_uniform(rng, 2.0 ** -40, 2.0 ** 40, (nx, ny, nz)) for _ in range(3)]
+        wind[2][:, :, -1] = 0.0
+    else:
+        wind = synthetic.wind_fields(nx, ny, nz, 25)
+    phi = _log_uniform(rng, lo, hi, (nx, ny, nz))
     got = run_scalars(pw, m, wind, [phi])
-    ref, cond = oracle.advect_scalar(oracle.Coeffs(nz, 50.0, 50.0), *wind, phi, want_cond=True)
-    compare("s", got[0], ref, cond, TOL_F64, TOL_F64)
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    ref, cond = oracle.advect_scalar(c, *wind, phi, want_cond=True)
+    ones = np.ones((nx, ny, nz))
+    _, q1 = oracle.advect_scalar(c, ones, ones, ones, ones, want_cond=True)
+    a = np.maximum.reduce([np.abs(x) for x in list(wind) + [phi]])
+    for ax in (0, 1):
+        a = np.maximum.reduce([a, np.roll(a, 1, ax), np.roll(a, -1, ax)])
+    a = np.maximum.reduce([a, np.concatenate([a[:, :, 1:], a[:, :, -1:]], 2),
+                           np.concatenate([a[:, :, :1], a[:, :, :-1]], 2)])
+    err = np.abs(got[0] - ref)
+    lim = 1e-12 * cond + 2.0 ** -100 * 2 * a * q1 + 2.0 ** -140
+    assert np.all(err <= lim), float((err - lim).max())
+    assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("bad", ["huge_scalar", "nan_scalar", "inf_scalar", "huge_wind"])
+def test_split_scalars_out_of_range_is_reported(pw, bad):
+    """A scalar at or above 2^60 in magnitude (or NaN, Inf), or a wind at or
+    above 2^40, sets PW_ERR_RANGE."""
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz = 17, 15, 12
+    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64", algo="split")
+    wind = list(synthetic.wind_fields(nx, ny, nz, 27))
+    phi = synthetic.scalar_fields(nx, ny, nz, 1, 28)[0]
+    value = {"huge_scalar": 2.0 ** 60, "nan_scalar": np.nan, "inf_scalar": -np.inf, "huge_wind": 2.0 ** 40}[bad]
+    if bad == "huge_wind":
+        wind[1][8, 7, 4] = value
+    else:
+        phi[8, 7, 4] = value
+    U = [m.from_interior(a) for a in wind]
+    m.advect_scalars(*U, [m.from_interior(phi)])
+    torch.cuda.synchronize()
+    assert m.device_status() == L.PW_ERR_RANGE
+    assert m.device_status() == 0

@@ -94,3 +94,15 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def test_residual_ratios_host_arithmetic(lib):
+    """pw_residual_ratios is pure host arithmetic: R_E = sum W phi S / sum W |phi S|,
+    R_M = sum W S / sum W |S| per component, 0 for a zero denominator."""
+    sums = [1.0, 4.0, -3.0, 6.0, 0.0, 0.0, 2.0, 8.0, -5.0, 10.0, 0.5, 0.0]
+    r = lib.pw_residual_ratios(sums)
+    assert r == [0.25, 0.0, -0.5, -0.5, 0.25, 0.0]
+    c = lib._c
+    assert c.pw_residual_ratios(None, None) == lib.PW_ERR_ARG
+    assert c.pw_mesh_algo(ctypes.c_void_p(0), None) == lib.PW_ERR_ARG
+    assert "split" in lib.status_string(lib.PW_ERR_RANGE)

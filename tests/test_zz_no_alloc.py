@@ -29,15 +29,15 @@ def pw():
 
 def _noalloc(L, m, U, S, stream):
     c = m.coefficients()
-    out = L.pw_residuals_noalloc(m.nx, m.ny, m.nz, m.nzp, {"f64": L.PW_F64, "f32": L.PW_F32,
-                                                              "bf16": L.PW_BF16}[m.dtype],
+    out = L.pw_residuals_noalloc(m.nx, m.ny, m.nz, m.nzp, {"f64": L.PW_F64, "f32": L.PW_F32, "bf16": L.PW_BF16,
+                                                              "bf16_out": L.PW_BF16_OUT}[m.dtype],
                                  list(c["W_uv"]), list(c["W_w"]),
                                  *(ctypes.c_void_p(t.data_ptr()) for t in U),
                                  *(ctypes.c_void_p(t.data_ptr()) for t in S), stream)
     return np.array(out).reshape(3, 4)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "bf16_out"])
 def test_noalloc_matches_residuals_twice(pw, dtype):
     from paper_2009_12850_b300 import _lib as L
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -68,3 +68,22 @@ def test_noalloc_rejects_oversized_columns(pw):
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert e.value.status == L.PW_ERR_SHAPE
     assert "PW_NOALLOC_MAX_NZ" in str(e.value)
+
+
+def test_noalloc_refuses_host_memory(pw):
+    """A pinned host buffer in place of a device field is refused before any
+    launch (PW_ERR_ARG), as is a weight list of the wrong length."""
+    from paper_2009_12850_b300 import _lib as L
+    m = pw.Mesh(8, 8, 8, 50.0, dtype="f32")
+    U = [m.zeros() for _ in range(3)]
+    S = [m.empty_out() for _ in range(3)]
+    host = torch.zeros(m.shape, dtype=torch.float32, pin_memory=True)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in U + S]
+    ptrs[1] = ctypes.c_void_p(host.data_ptr())
+    with pytest.raises(L.PWError) as e:
+        L.pw_residuals_noalloc(8, 8, 8, m.nzp, L.PW_F32, [1.0] * 8, [1.0] * 8, *ptrs, stream)
+    assert e.value.status == L.PW_ERR_ARG and "v is not device memory" in str(e.value)
+    with pytest.raises(ValueError):
+        L.pw_residuals_noalloc(8, 8, 8, m.nzp, L.PW_F32, [1.0] * 7, [1.0] * 8,
+                               *(ctypes.c_void_p(t.data_ptr()) for t in U + S), stream)
