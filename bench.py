@@ -299,9 +299,8 @@ def run_gpu(args):
         for _ in range(nres):
             sums = m64.residual_sums(*U64, *S64)
         dt = (time.perf_counter() - t0) / nres
-        re = [float(sums[q, 0] / sums[q, 1]) for q in range(3)]
-        rm = [float(sums[q, 2] / sums[q, 3]) for q in range(3)]
-        extras["residuals"] = {"ms_per_call": round(dt * 1e3, 3), "R_E": re, "R_M": rm}
+        re, rm = m64.residuals(*U64, *S64)
+        extras["residuals"] = {"ms_per_call": round(dt * 1e3, 3), "R_E": list(re), "R_M": list(rm)}
 
     for name, fn in (("small_latency", lambda: bench_small_latency(args, world)),
                      ("scalars", lambda: bench_scalars(args, world, hbm)),
@@ -361,6 +360,9 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        pv = precision_vs_oracle()
+        if pv is not None and "precision" in extras:
+            extras["precision"]["error_vs_oracle"] = pv
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -544,7 +546,10 @@ def bench_fused_step(args, world, hbm):
     update (pw_advect_step, halos of the new state written in the same pass)
     against halo fill + pw_advect + pw_euler; and the whole advection step of
     the wind with theta + 5 q (pw_advect_step + pw_advect_scalars_step against
-    halos + both stencils + three pw_euler passes)."""
+    halos + both stencils + three pw_euler passes).  Every timed step starts
+    from the same state (the new state goes to a second buffer), so the work
+    per step is exactly one step of the initial fields: hundreds of chained
+    advection-only Euler steps would let the state grow without bound."""
     import torch
     from paper_2009_12850_b300 import api
     out = {"workload": WL.name, "dt": 0.5}
@@ -555,19 +560,18 @@ def bench_fused_step(args, world, hbm):
         m = api.Mesh(WL.nx, WL.ny, WL.nz, WL.dx, WL.dy, dtype=dtype)
         A = [m.from_interior(a) for a in f]
         B = [m.empty() for _ in range(3)]
-        cur = [A, B]
 
         def fused(rec):
-            m.step(*cur[0], *cur[1], dt=0.5)
-            cur.reverse()
+            m.step(*A, *B, dt=0.5)
         steps = max(3, args.steps // 2)
         tf, _ = time_steps(fused, steps, 3, world)
         S = [m.empty_out() for _ in range(3)]
+        E = [t.clone() for t in A]   # the update target of the unfused sequence
 
         def unfused(rec):
             m.halo(*A)
             m.advect(*A, *S)
-            m.euler(*A, *S, 0.5)
+            m.euler(*E, *S, 0.5)
         tu, _ = time_steps(unfused, steps, 3, world)
         assert m.device_status() == 0
         es = {"f64": 8, "f32": 4}[dtype]
@@ -578,15 +582,13 @@ def bench_fused_step(args, world, hbm):
         # the whole advection step of the wind and theta + 5 q (old wind for all)
         P = [m.from_interior(a) for a in phis]
         Q = [m.empty() for _ in range(6)]
-        pcur = [P, Q]
 
         def fused_all(rec):
-            m.step(*cur[0], *cur[1], dt=0.5)
-            m.step_scalars(*cur[0], pcur[0], pcur[1], dt=0.5)
-            cur.reverse()
-            pcur.reverse()
+            m.step(*A, *B, dt=0.5)
+            m.step_scalars(*A, P, Q, dt=0.5)
         tfa, _ = time_steps(fused_all, steps, 3, world)
         SP = [m.empty_out() for _ in range(6)]
+        EP = [t.clone() for t in P]
 
         def unfused_all(rec):
             m.halo(*A)
@@ -594,16 +596,16 @@ def bench_fused_step(args, world, hbm):
             m.halo(*P[3:])
             m.advect(*A, *S)
             m.advect_scalars(*A, P, SP)
-            m.euler(*A, *S, 0.5)
-            m.euler(*P[:3], *SP[:3], 0.5)
-            m.euler(*P[3:], *SP[3:], 0.5)
+            m.euler(*E, *S, 0.5)
+            m.euler(*EP[:3], *SP[:3], 0.5)
+            m.euler(*EP[3:], *SP[3:], 0.5)
         tua, _ = time_steps(unfused_all, steps, 3, world)
         assert m.device_status() == 0
         out[dtype]["wind_theta_5q"] = {"fused_ms": round(tfa / steps * 1e3, 4),
                                        "unfused_ms": round(tua / steps * 1e3, 4), "speedup": round(tua / tfa, 3),
                                        "fused_bytes_per_point": (6 + 15) * es,
                                        "unfused_bytes_per_point": (15 + 3 + 6 * 5) * es}
-        del m, A, B, S, cur, P, Q, SP, pcur
+        del m, A, B, S, E, P, Q, SP, EP
         torch.cuda.empty_cache()
     return out
 
@@ -649,7 +651,7 @@ def bench_adjoint_loop(args):
     dt, steps, every = wl.extra["dt"], wl.extra["steps"], wl.extra["checkpoint_every"]
     out = {}
     grads = {}
-    for dtype, algo in (("f32", "auto"), ("f64", "native")):
+    for dtype, algo in (("f32", "auto"), ("f64", "auto"), ("f64", "native")):
         m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype, algo=algo)
         base = [m.from_interior(a) for a in f]
 
@@ -671,7 +673,8 @@ def bench_adjoint_loop(args):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         res = {"ms_per_loss_and_grad_eager_median": round(float(np.median(times)), 3), "loss": float(L.item())}
-        grads[dtype] = [m.interior(u.grad).double() for u in U]
+        key = dtype if algo == "auto" else dtype + "_native"
+        grads[key] = [m.interior(u.grad).double() for u in U]
         # the same loss and gradient captured in one CUDA graph and replayed: the
         # device-side time of the whole computation, free of launch overhead
         Ug = [t.clone().requires_grad_(True) for t in base]
@@ -695,12 +698,15 @@ def bench_adjoint_loop(args):
         torch.cuda.synchronize()
         assert m.device_status() == 0
         res["ms_per_loss_and_grad"] = round(e0.elapsed_time(e1) / n, 3)
-        out[dtype] = res
+        out[key] = res
         del m, base, U, Ug, graph
-    rel = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(grads["f32"], grads["f64"])]
+    rel = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(grads["f32"], grads["f64_native"])]
+    rel2 = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(grads["f64"], grads["f64_native"])]
     return {"workload": wl.name, "steps": steps, "dt": dt, "checkpoint_every": every,
-            "f32": out["f32"], "f64_native": out["f64"],
-            "grad_rel_err_f32_vs_f64": {"gu": rel[0], "gv": rel[1], "gw": rel[2]}}
+            "f32": out["f32"], "f64": out["f64"], "f64_native": out["f64_native"],
+            "f64_note": "f64: double-float forward steps with the native FP64 adjoint; f64_native: native FP64 throughout",
+            "grad_rel_err_f32_vs_f64": {"gu": rel[0], "gv": rel[1], "gw": rel[2]},
+            "grad_rel_err_f64_vs_f64_native": {"gu": rel2[0], "gv": rel2[1], "gw": rel2[2]}}
 
 
 def bench_adjoint_kernel(args):
@@ -740,32 +746,30 @@ def bench_adjoint_kernel(args):
 
 
 def bench_precision():
-    """512 x 512 x 160 sheared turbulence: FP32 and BF16 storage against the
-    FP64 split path (itself within 1e-12 of the oracle), max and RMS error per
-    source, and the conservation residuals of each."""
+    """512 x 512 x 160 sheared turbulence: the sources in FP64 (split), FP32,
+    BF16 and BF16-in-and-out storage, and the conservation residuals of each.
+    The sources are kept in host memory; their max and RMS error against the
+    FP64 oracle is filled in by the CPU leg (precision_vs_oracle), which is the
+    only part of this program that runs the oracle."""
     import torch
     from paper_2009_12850_b300 import api
     wl = synthetic.PRECISION
     f = synthetic.fields_for(wl)
-    res = {}
-    ref = None
-    for dtype in ("f64", "f32", "bf16"):
+    res, kept = {}, {}
+    for dtype in ("f64", "f32", "bf16", "bf16_out"):
         m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype)
         U = [m.from_interior(a) for a in f]
         S = m.advect(*U)
-        sums = m.residual_sums(*U, *S)
-        entry = {"R_E": [float(sums[q, 0] / sums[q, 1]) for q in range(3)],
-                 "R_M": [float(sums[q, 2] / sums[q, 3]) for q in range(3)]}
-        if dtype == "f64":
-            ref = [m.interior(t).clone() for t in S]
-        else:
-            for q, nm in enumerate(("su", "sv", "sw")):
-                d = (m.interior(S[q]).double() - ref[q]).abs()
-                entry[nm] = {"max_abs": float(d.max()), "rms": float(d.pow(2).mean().sqrt()),
-                             "max_rel_to_max": float(d.max() / ref[q].abs().max())}
-        res[dtype] = entry
+        re, rm = m.residuals(*U, *S)
+        assert m.device_status() == 0
+        res[dtype] = {"R_E": list(re), "R_M": list(rm)}
+        kept[dtype] = [m.interior(t).double().cpu().numpy() for t in S]
         del m, U, S
+    PRECISION_KEPT["sources"] = kept
     return {"workload": wl.name, "fields": "u = 15 z/z_top + N(0,2), v = N(0,2), w = N(0,0.3) m/s", **res}
+
+
+PRECISION_KEPT = {}
 
 
 # ----------------------------------------------------------------------------
@@ -801,6 +805,31 @@ def cpu_model():
     except OSError:
         pass
     return platform.processor() or "unknown"
+
+
+def precision_vs_oracle():
+    """Max and RMS error, per source, of the precision row's GPU sources against
+    the FP64 oracle evaluated on the original (unrounded) FP64 fields, also
+    relative to each point's condition sum."""
+    import oracle
+    kept = PRECISION_KEPT.pop("sources", None)
+    if not kept:
+        return None
+    wl = synthetic.PRECISION
+    f = synthetic.fields_for(wl)
+    c = oracle.Coeffs(wl.nz, wl.dx, wl.dy)
+    ref, cond = oracle.advect(c, *f, want_cond=True)
+    out = {"reference": "FP64 oracle on the unrounded fields"}
+    for dtype, S in kept.items():
+        e = {}
+        for q, nm in enumerate(("su", "sv", "sw")):
+            d = np.abs(S[q] - ref[q])
+            with np.errstate(divide="ignore", invalid="ignore"):
+                r = np.where(cond[q] > 0, d / cond[q], 0.0)
+            e[nm] = {"max_abs": float(d.max()), "rms": float(np.sqrt(np.mean(d * d))),
+                     "max_rel_to_max": float(d.max() / np.abs(ref[q]).max()), "max_err_over_cond": float(r.max())}
+        out[dtype] = e
+    return out
 
 
 def cpu_baseline(seconds):
@@ -847,6 +876,18 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_fp_rates():
+    """Compile and run the package's arithmetic-rate microbenchmark
+    (paper_2009_12850_b300/rates/fp_rates.cu): the FP64, conversion and FP32
+    rates that decide how the FP64 stencil computes.  Prints its JSON line."""
+    src = os.path.join(ROOT, "paper_2009_12850_b300", "rates", "fp_rates.cu")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "fp_rates")
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    print(json.dumps({"fp_rates": json.loads(out)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -864,6 +905,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16", "bf16_out"], default="f64", help="headline storage type")
     ap.add_argument("--algo", choices=["auto", "native", "split"], default="auto", help="FP64 arithmetic")
+    ap.add_argument("--fp-rates", action="store_true",
+                    help="only run the arithmetic-rate microbenchmark (FP64, f64<->f32, FP32, FP32x2) and print it")
     ap.add_argument("--nx", type=int, default=None, help="smaller domain (ncu captures)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -874,7 +917,9 @@ def main():
         WL = synthetic.Workload(f"pw_{nx}x{ny}x{nz}_dx25", nx, ny, nz, WL.dx, WL.dy, WL.seed)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.impl == "reference":
+    if args.fp_rates:
+        run_fp_rates()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

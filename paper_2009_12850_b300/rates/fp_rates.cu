@@ -1,4 +1,4 @@
-// Throughput probe of the arithmetic the FP64 design depends on: FP64 FMA and
+// Rate microbenchmark of the arithmetic the FP64 design depends on: FP64 FMA and
 // add, f64<->f32 conversions, FP32 FMA and packed FP32x2 FMA.  Each kernel runs
 // 8 independent dependency chains per thread over 8 CTAs per SM; results are
 // written only under a runtime flag that is 0, so nothing is optimised away.

@@ -88,7 +88,7 @@ def test_adjoint_loop_full_size_gradients(pw, loop_fields):
     # inputs to FP32 moves the gradient by ~1e-7 relative, far inside the FP32 bound
     c = oracle.Coeffs(NZ, 50.0, 50.0)
     Lref, gref = oracle.loss_and_grad(c, *loop_fields, DT, STEPS)
-    for dtype, algo, tol in (("f32", "auto", 1e-5), ("f64", "native", 1e-10)):
+    for dtype, algo, tol in (("f32", "auto", 1e-5), ("f64", "native", 1e-10), ("f64", "split", 1e-10)):
         m = pw.Mesh(NX, NY, NZ, 50.0, dtype=dtype, algo=algo)
         U = [m.from_interior(a).requires_grad_(True) for a in loop_fields]
         L = AG.source_energy_loss(m, *U, dt=DT, steps=STEPS, checkpoint_every=2)
