@@ -23,7 +23,7 @@ struct pw_mesh {
     double *coef64;          // device, 12*nz: dz zf zn dzn rho_n rho_w tzc1 tzc2 tzd1 tzd2 Wuv Ww
     float *coef32;           // device, 4*nz: tzc1 tzc2 tzd1 tzd2
     float *coefsplit;        // device, 8*(nz+4)+4: float pairs of g, g', r, r' (levels -2..nz+1), tcx, tcy
-    double *partials;        // device, residual scratch: (PW_RED_BLOCKS + 1) * 12 doubles
+    double *partials;        // device, residual scratch: PW_RED_SCRATCH doubles
     int *status;             // device: [0] timeout status (0 or PW_ERR_TIMEOUT), [1] lid flag,
                              // [2] split-range flag, [3] unused
     int tile_j, tile_i;      // stencil tile: rows per CTA, columns marched per CTA
@@ -33,9 +33,14 @@ struct pw_mesh {
 #define PW_STATUS_WORDS 4
 #define PW_STATUS_RANGE_WORD 2  // set by the split kernels when a value was outside their range
 
-// reduction geometry of pw_residuals (fixed so the order of sums is fixed)
+// reduction geometry of pw_residuals (fixed so the order of sums is fixed):
+// PW_RED_BLOCKS blocks each write PW_RED_STRIDE doubles (the 12 sums and a
+// count of values outside the fast path's range), then PW_RED_STRIDE totals
 #define PW_RED_BLOCKS 592
 #define PW_RED_THREADS 256
+#define PW_RED_FAST_THREADS 128
+#define PW_RED_STRIDE 13
+#define PW_RED_SCRATCH ((PW_RED_BLOCKS + 1) * PW_RED_STRIDE)
 
 // bounded waits: ~1 s at 2 GHz for a copy the kernel needs; ~50 ms when a
 // kernel that already gave up drains copies still in flight.  On expiry the
@@ -85,13 +90,18 @@ pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *
                                    const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
                                    int tile_j, int tile_i, int group);
 pw_status pw_launch_halo(const pw_mesh *m, void *const *f, int nf, cudaStream_t st);
-pw_status pw_launch_residuals_raw(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
-                                  const double *ww, const void *u, const void *v, const void *w,
-                                  const void *su, const void *sv, const void *sw, double *partials,
-                                  double *dout, cudaStream_t st);
-pw_status pw_launch_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
-                              const void *su, const void *sv, const void *sw, double *partials,
-                              double *dout, cudaStream_t st);
+// FP64 adjoint in double-float arithmetic (pw_adjoint_split.cu): in = u, v, w,
+// gsu, gsv, gsw (halos of the gradients filled), out = gu, gv, gw.
+pw_status pw_launch_adjoint_split(const pw_mesh *m, const void *const *in, void *const *out, double alpha,
+                                  int beta, int add_y, cudaStream_t st);
+
+// The conservation sums (pw_residuals.cu): the 12 sums into the HOST array
+// out, computed on `st` with `scratch` (PW_RED_SCRATCH device doubles) and the
+// energy weights wuv, ww (device, nz each); synchronises `st`.
+pw_status pw_residuals_run(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
+                           const double *ww, const void *u, const void *v, const void *w,
+                           const void *su, const void *sv, const void *sw, double *scratch,
+                           double *out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device helpers

@@ -253,7 +253,7 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
     if ((e = cudaMalloc(&m->coef64, 12 * (size_t)nz * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&m->coef32, 4 * (size_t)nz * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&m->coefsplit, (8 * ((size_t)nz + 4) + 4) * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&m->partials, (PW_RED_BLOCKS + 1) * 12 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&m->partials, PW_RED_SCRATCH * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&m->status, PW_STATUS_WORDS * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&tmp, 3 * (size_t)nz * sizeof(double))) != cudaSuccess) {
         pw_mesh_free(m);
@@ -585,139 +585,6 @@ extern "C" pw_status pw_euler(const pw_mesh *m, void *u, void *v, void *w, const
     else
         return pw_fail(PW_ERR_DTYPE, "pw_euler supports PW_F64 and PW_F32 meshes");
     PW_CUDA(cudaGetLastError());
-    return PW_OK;
-}
-
-// ---------------------------------------------------------------------------
-// A5: FP64 conservation sums, deterministic two-pass tree reduction
-// ---------------------------------------------------------------------------
-template <typename TF, typename TS>
-__global__ void __launch_bounds__(PW_RED_THREADS)
-pw_residual_pass1(const TF *u, const TF *v, const TF *w, const TS *su, const TS *sv, const TS *sw,
-                  const double *wuv, const double *ww, int nx, int ny, int nz, int nzp,
-                  double *partials) {
-    __shared__ double red[12][PW_RED_THREADS];
-    double acc[12];
-#pragma unroll
-    for (int q = 0; q < 12; q++) acc[q] = 0.0;
-    int64_t n = (int64_t)nx * ny * nz;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-        int k = (int)(e % nz);
-        int64_t col = e / nz;
-        int j = (int)(col % ny), i = (int)(col / ny);
-        int64_t off = ((int64_t)(i + 2) * (ny + 4) + (j + 2)) * nzp + k;
-        double Wc[3] = {wuv[k], wuv[k], ww[k]};
-        double f[3] = {pw_to<double>(u[off]), pw_to<double>(v[off]), pw_to<double>(w[off])};
-        double s[3] = {pw_to<double>(su[off]), pw_to<double>(sv[off]), pw_to<double>(sw[off])};
-        if (k == nz - 1) {  // lid face: w and sw are 0 by definition
-            f[2] = 0.0;
-            s[2] = 0.0;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            double ps = f[c] * s[c];
-            acc[4 * c + 0] += Wc[c] * ps;
-            acc[4 * c + 1] += Wc[c] * fabs(ps);
-            acc[4 * c + 2] += Wc[c] * s[c];
-            acc[4 * c + 3] += Wc[c] * fabs(s[c]);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 12; q++) red[q][threadIdx.x] = acc[q];
-    __syncthreads();
-    for (int h = PW_RED_THREADS / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h)
-            for (int q = 0; q < 12; q++) red[q][threadIdx.x] += red[q][threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x < 12) partials[(int64_t)blockIdx.x * 12 + threadIdx.x] = red[threadIdx.x][0];
-}
-
-__global__ void __launch_bounds__(PW_RED_THREADS)
-pw_residual_pass2(const double *partials, int nblocks, double *out) {
-    __shared__ double red[12][PW_RED_THREADS];
-    for (int q = 0; q < 12; q++) {
-        double a = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partials[(int64_t)b * 12 + q];
-        red[q][threadIdx.x] = a;
-    }
-    __syncthreads();
-    for (int h = PW_RED_THREADS / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h)
-            for (int q = 0; q < 12; q++) red[q][threadIdx.x] += red[q][threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x < 12) out[threadIdx.x] = red[threadIdx.x][0];
-}
-
-// Launch both passes; `partials` holds PW_RED_BLOCKS*12 doubles and `dout`
-// 12 doubles (both device memory).
-pw_status pw_launch_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
-                              const void *su, const void *sv, const void *sw, double *partials,
-                              double *dout, cudaStream_t st) {
-    const double *wuv = m->coef64 + 10 * m->nz, *ww = m->coef64 + 11 * m->nz;
-#define PW_RES(TF, TS)                                                                         \
-    pw_residual_pass1<TF, TS><<<PW_RED_BLOCKS, PW_RED_THREADS, 0, st>>>(                       \
-        (const TF *)u, (const TF *)v, (const TF *)w, (const TS *)su, (const TS *)sv,           \
-        (const TS *)sw, wuv, ww, m->nx, m->ny, m->nz, m->nzp, partials)
-    if (m->dtype == PW_F64) PW_RES(double, double);
-    else if (m->dtype == PW_F32) PW_RES(float, float);
-    else if (m->dtype == PW_BF16_OUT) PW_RES(__nv_bfloat16, __nv_bfloat16);
-    else PW_RES(__nv_bfloat16, float);
-#undef PW_RES
-    PW_CUDA(cudaGetLastError());
-    pw_residual_pass2<<<1, PW_RED_THREADS, 0, st>>>(partials, PW_RED_BLOCKS, dout);
-    PW_CUDA(cudaGetLastError());
-    return PW_OK;
-}
-
-// Same two passes for callers that hold the layout and the weights themselves
-// (no mesh): used by the entry point whose scratch is a static device array.
-pw_status pw_launch_residuals_raw(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
-                                  const double *ww, const void *u, const void *v, const void *w,
-                                  const void *su, const void *sv, const void *sw, double *partials,
-                                  double *dout, cudaStream_t st) {
-#define PW_RES_RAW(TF, TS)                                                                     \
-    pw_residual_pass1<TF, TS><<<PW_RED_BLOCKS, PW_RED_THREADS, 0, st>>>(                       \
-        (const TF *)u, (const TF *)v, (const TF *)w, (const TS *)su, (const TS *)sv,           \
-        (const TS *)sw, wuv, ww, nx, ny, nz, nzp, partials)
-    if (dtype == PW_F64) PW_RES_RAW(double, double);
-    else if (dtype == PW_F32) PW_RES_RAW(float, float);
-    else if (dtype == PW_BF16_OUT) PW_RES_RAW(__nv_bfloat16, __nv_bfloat16);
-    else PW_RES_RAW(__nv_bfloat16, float);
-#undef PW_RES_RAW
-    PW_CUDA(cudaGetLastError());
-    pw_residual_pass2<<<1, PW_RED_THREADS, 0, st>>>(partials, PW_RED_BLOCKS, dout);
-    PW_CUDA(cudaGetLastError());
-    return PW_OK;
-}
-
-extern "C" pw_status pw_residuals(const pw_mesh *m, const void *u, const void *v, const void *w,
-                                  const void *su, const void *sv, const void *sw, double *out,
-                                  void *stream) {
-    if (!m || !out) return pw_fail(PW_ERR_ARG, "mesh and out must not be NULL");
-    pw_status s;
-    const void *ps[6] = {u, v, w, su, sv, sw};
-    const char *nm[6] = {"u", "v", "w", "su", "sv", "sw"};
-    for (int q = 0; q < 6; q++)
-        if ((s = pw_check_ptr(ps[q], nm[q])) != PW_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    // scratch: PW_RED_BLOCKS*12 block partials, then the 12 final sums
-    double *final_sums = m->partials + PW_RED_BLOCKS * 12;
-    if ((s = pw_launch_residuals(m, u, v, w, su, sv, sw, m->partials, final_sums, st)) != PW_OK)
-        return s;
-    PW_CUDA(cudaMemcpyAsync(out, final_sums, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    PW_CUDA(cudaStreamSynchronize(st));
-    return PW_OK;
-}
-
-extern "C" pw_status pw_residual_ratios(const double *sums, double *out) {
-    if (!sums || !out) return pw_fail(PW_ERR_ARG, "sums and out must not be NULL");
-    for (int c = 0; c < 3; c++) {
-        out[c] = sums[4 * c + 1] != 0.0 ? sums[4 * c] / sums[4 * c + 1] : 0.0;
-        out[3 + c] = sums[4 * c + 3] != 0.0 ? sums[4 * c + 2] / sums[4 * c + 3] : 0.0;
-    }
     return PW_OK;
 }
 

@@ -10,10 +10,11 @@
 // and the library uses a file-scope device array as its only scratch.
 #include "pw_internal.h"
 
-// Scratch: PW_RED_BLOCKS*12 block partials, 12 final sums, then the two weight
-// columns (PW_NOALLOC_MAX_NZ doubles each).  Every GPU that loads the library
-// holds this array (about 120 KB) until the process exits.
-static __device__ __align__(256) double pw_noalloc_scratch[(PW_RED_BLOCKS + 1) * 12 + 2 * PW_NOALLOC_MAX_NZ];
+// Scratch: the reduction records (PW_RED_SCRATCH doubles: the block partials
+// and the totals), then the two weight columns (PW_NOALLOC_MAX_NZ doubles each).
+// Every GPU that loads the library holds this array (about 125 KB) until the
+// process exits.
+static __device__ __align__(256) double pw_noalloc_scratch[PW_RED_SCRATCH + 2 * PW_NOALLOC_MAX_NZ];
 
 // Device address of the scratch array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address must come from
@@ -74,15 +75,12 @@ extern "C" pw_status pw_residuals_noalloc(int nx, int ny, int nz, int nzp, pw_dt
     double *scratch = nullptr;
     pw_status s = pw_noalloc_scratch_ptr(&scratch);
     if (s != PW_OK) return s;
-    double *partials = scratch;                         // every entry rewritten by pass 1
-    double *final_sums = scratch + PW_RED_BLOCKS * 12;  // rewritten by pass 2
-    double *wuv = final_sums + 12, *ww = wuv + PW_NOALLOC_MAX_NZ;
+    // every entry of the reduction records is rewritten by each pass
+    double *wuv = scratch + PW_RED_SCRATCH, *ww = wuv + PW_NOALLOC_MAX_NZ;
     cudaStream_t st = (cudaStream_t)stream;
     PW_CUDA(cudaMemcpyAsync(wuv, w_uv, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, st));
     PW_CUDA(cudaMemcpyAsync(ww, w_w, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, st));
-    s = pw_launch_residuals_raw(nx, ny, nz, nzp, dtype, wuv, ww, u, v, w, su, sv, sw, partials, final_sums, st);
+    s = pw_residuals_run(nx, ny, nz, nzp, dtype, wuv, ww, u, v, w, su, sv, sw, scratch, out, st);
     if (s != PW_OK) return s;
-    PW_CUDA(cudaMemcpyAsync(out, final_sums, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    PW_CUDA(cudaStreamSynchronize(st));
     return PW_OK;
 }

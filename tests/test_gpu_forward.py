@@ -208,6 +208,38 @@ def test_residual_sums(pw, dtype):
         assert max(abs(r) for r in re) < 1e-13
 
 
+@pytest.mark.parametrize("case", ["huge", "tiny", "subnormal", "mixed_wide"])
+def test_residual_sums_outside_fast_range(pw, case):
+    """Fields the double-float pass cannot carry (|x| from 2^56 up, nonzero
+    values below 2^-100, or sums of magnitudes below 2^-40) still give the FP64
+    sums: the library recomputes them in plain FP64.  Native FP64 stencil, so
+    the sources are the oracle's to 1e-12."""
+    nx, ny, nz = 21, 18, 13
+    m, f = make(pw, nx, ny, nz, algo="native")
+    f = [a.copy() for a in f]
+    rng = np.random.default_rng(5)
+    if case == "huge":
+        f[0][3, 4, 5] = 2.0 ** 60
+    elif case == "tiny":
+        f = [a * 1e-35 for a in f]
+    elif case == "subnormal":
+        f[1][2, 2, 2] = 5e-324
+    else:
+        f = [a * np.exp2(rng.uniform(-30, 30, a.shape)) for a in f]
+    f[2][:, :, -1] = 0.0
+    U = [m.from_interior(a) for a in f]
+    S = m.advect(*U)
+    gsum = m.residual_sums(*U, *S)
+    c = oracle.Coeffs(nz, 50.0, 50.0)
+    sr = [m.interior(s).double().cpu().numpy() for s in S]
+    ref = oracle.residual_sums(c, *f, *sr)
+    for q in range(3):
+        for t in range(4):
+            den = ref[q, 1] if t < 2 else ref[q, 3]
+            assert abs(gsum[q, t] - ref[q, t]) <= 1e-13 * den, (case, q, t, gsum[q, t], ref[q, t])
+    assert np.array_equal(gsum, m.residual_sums(*U, *S))
+
+
 def test_argument_errors_on_device(pw):
     from paper_2009_12850_b300 import _lib as L
     m = pw.Mesh(8, 8, 8, 50.0, dtype="f32")
