@@ -704,44 +704,49 @@ def bench_adjoint_loop(args):
     rel2 = [float((a - b).abs().max() / b.abs().max()) for a, b in zip(grads["f64"], grads["f64_native"])]
     return {"workload": wl.name, "steps": steps, "dt": dt, "checkpoint_every": every,
             "f32": out["f32"], "f64": out["f64"], "f64_native": out["f64_native"],
-            "f64_note": "f64: double-float forward steps with the native FP64 adjoint; f64_native: native FP64 throughout",
+            "f64_note": "f64: double-float (split) forward steps and adjoint; f64_native: native FP64 throughout",
             "grad_rel_err_f32_vs_f64": {"gu": rel[0], "gv": rel[1], "gw": rel[2]},
             "grad_rel_err_f64_vs_f64_native": {"gu": rel2[0], "gv": rel2[1], "gw": rel2[2]}}
 
 
 def bench_adjoint_kernel(args):
-    """The adjoint stencil alone on the bandwidth workload (1024 x 1024 x 128,
-    FP32): gu, gv, gw = J(u,v,w)^T (gsu, gsv, gsw), 6 fields read and 3 written
-    (36 B/point compulsory)."""
+    """The adjoint stencil alone on the bandwidth workload (1024 x 1024 x 128):
+    gu, gv, gw = J(u,v,w)^T (gsu, gsv, gsw), 6 fields read and 3 written
+    (36 B/point compulsory in FP32, 72 in FP64), in FP32 and in FP64
+    (double-float arithmetic)."""
     import torch
     from paper_2009_12850_b300 import api
     wl = WL
-    m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype="f32")
-    U = [m.from_interior(a) for a in synthetic.fields_for(wl)]
-    Y = [m.zeros() for _ in range(3)]
-    for t in Y:
-        t.normal_()
-    G = [m.zeros() for _ in range(3)]
-    stream = torch.cuda.current_stream()
-
-    def step(rec):
-        if rec is None:
-            m.adjoint(*U, *Y, *G, stream=stream)
-            return
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        m.adjoint(*U, *Y, *G, stream=stream)
-        b.record(stream)
-        rec.append((a, b))
-    steps = max(3, args.steps // 2)
-    _, kms = time_steps(step, steps, 3, world_size())
-    assert m.device_status() == 0
-    pts = wl.points
     peak = float(load_peaks()[0]["hbm_gbs"])
-    out = {"workload": wl.name, "dtype": "f32", "ms_per_call": round(kms, 4), "value": pts / (kms * 1e-3),
-           "unit": UNIT, "bytes_per_point": 36, "hbm_frac": round(36 * pts / (kms * 1e-3) / 1e9 / peak, 4)}
-    del m, U, Y, G
-    torch.cuda.empty_cache()
+    out = {"workload": wl.name}
+    for dtype in ("f32", "f64"):
+        m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype)
+        U = [m.from_interior(a) for a in synthetic.fields_for(wl)]
+        Y = [m.zeros() for _ in range(3)]
+        for t in Y:
+            t.normal_()
+        G = [m.zeros() for _ in range(3)]
+        stream = torch.cuda.current_stream()
+
+        def step(rec):
+            if rec is None:
+                m.adjoint(*U, *Y, *G, stream=stream)
+                return
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.adjoint(*U, *Y, *G, stream=stream)
+            b.record(stream)
+            rec.append((a, b))
+        steps = max(3, args.steps // 2)
+        _, kms = time_steps(step, steps, 3, world_size())
+        assert m.device_status() == 0
+        pts = wl.points
+        bpp = 36 if dtype == "f32" else 72
+        out[dtype] = {"ms_per_call": round(kms, 4), "value": pts / (kms * 1e-3), "unit": UNIT,
+                      "bytes_per_point": bpp, "hbm_frac": round(bpp * pts / (kms * 1e-3) / 1e9 / peak, 4),
+                      "algo": m.algo}
+        del m, U, Y, G
+        torch.cuda.empty_cache()
     return out
 
 

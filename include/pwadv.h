@@ -328,7 +328,8 @@ pw_status pw_advect_host_scalars(pw_pipeline *p, const void *u, const void *v, c
  * THEIR HALO COLUMNS ARE OVERWRITTEN with periodic copies.  gw(.,.,nz-1) = 0
  * (the lid is not a degree of freedom).  Only interior points k < nz of
  * gu, gv, gw are written.  For nz = 1 (sw identically 0) gsw is ignored and
- * overwritten with 0.  FP32 and FP64 meshes (FP64 in native FP64 arithmetic);
+ * overwritten with 0.  FP32 and FP64 meshes (FP64 in the mesh's arithmetic: double-float
+ * on the FP32 pipe for PW_ALGO_F64_SPLIT, within its range, else native FP64);
  * PW_ERR_DTYPE for PW_BF16 and PW_BF16_OUT.  No argument may alias an output. */
 pw_status pw_advect_adjoint(const pw_mesh *mesh, const void *u, const void *v, const void *w,
                             void *gsu, void *gsv, void *gsw,
@@ -349,8 +350,14 @@ pw_status pw_euler_adjoint(const pw_mesh *mesh, const void *u, const void *v, co
 pw_status pw_euler(const pw_mesh *mesh, void *u, void *v, void *w,
                    const void *su, const void *sv, const void *sw, double dt, void *stream);
 
-/* Conservation diagnostics, accumulated in FP64 on the GPU with a deterministic
- * two-pass tree reduction (the order does not depend on timing).  With weights
+/* Conservation diagnostics with FP64 accuracy, from a deterministic two-pass
+ * tree reduction (the order does not depend on timing: repeated calls give the
+ * same bits).  The first pass accumulates double-float sums on the FP32 pipe
+ * (each sum within a few units of 2^-46 of the sum of its terms' magnitudes);
+ * if an input is outside what that pass carries exactly (a nonzero |x| below
+ * 2^-100 or from 2^56 up, NaN, Inf) or a sum of magnitudes is below 2^-40, the
+ * sums are recomputed in plain FP64, so the result never depends on the range
+ * of the data.  With weights
  * W = rho_n dz on u/v levels and rho_w dzn on w faces (lid face 0), for each
  * component c in (u, v, w) with source S:
  *   out[4c+0] = sum W phi S,   out[4c+1] = sum W |phi S|,
@@ -389,7 +396,7 @@ pw_status pw_residual_ratios(const double *sums, double *out);
  * array out of 12 doubles, filled exactly as by pw_residuals.
  *
  * Allocation: none.  The only scratch is a file-scope device array of about
- * 120 KB, held on every GPU that loads the library until the process exits.
+ * 127 KB, held on every GPU that loads the library until the process exits.
  * Every call looks up that array's device address (cudaGetSymbolAddress) with
  * the current device, so it stays right after a context is re-created; the
  * call synchronises `stream`, so it cannot sit inside a stream capture.  The six

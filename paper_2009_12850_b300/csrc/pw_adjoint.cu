@@ -294,6 +294,7 @@ static pw_status pw_adjoint_common(const pw_mesh *m, const void *u, const void *
     void *out[3] = {gu, gv, gw};
     if (m->dtype == PW_F32)
         return pw_launch_adjoint<float, float, 2>(m, in, out, alpha, beta, add_y, st, 4, m->tile_i, 4);
+    if (m->algo == PW_ALGO_F64_SPLIT) return pw_launch_adjoint_split(m, in, out, alpha, beta, add_y, st);
     return pw_launch_adjoint<double, double, 2>(m, in, out, alpha, beta, add_y, st, 4, m->tile_i, 4);
 }
 

@@ -20,8 +20,8 @@ def pw():
     return api
 
 
-def setup(pw, nx, ny, nz, dtype, seed=4):
-    m = pw.Mesh(nx, ny, nz, 50.0, 30.0, dtype=dtype, algo="native")
+def setup(pw, nx, ny, nz, dtype, seed=4, algo="native"):
+    m = pw.Mesh(nx, ny, nz, 50.0, 30.0, dtype=dtype, algo=algo)
     u, v, w = synthetic.wind_fields(nx, ny, nz, seed)
     rng = np.random.default_rng(seed + 100)
     y = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
@@ -47,10 +47,13 @@ def gpu_adjoint(m, f, y, alpha=1.0, beta=0, init=None):
 
 @pytest.mark.parametrize("shape", [(24, 20, 16), (37, 23, 13), (5, 7, 1), (1, 6, 5), (7, 1, 4), (3, 3, 2),
                                    (12, 10, 300)], ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_adjoint_matches_oracle(pw, shape, dtype):
+@pytest.mark.parametrize("dtype,algo", [("f64", "native"), ("f64", "split"), ("f32", "auto")])
+def test_adjoint_matches_oracle(pw, shape, dtype, algo):
+    """The FP64 adjoint in native FP64 and in double-float (split) arithmetic,
+    and the FP32 adjoint, against the oracle's transpose: 1e-12 normwise and of
+    each point's gradient condition sum for FP64."""
     nx, ny, nz = shape
-    m, f, y = setup(pw, nx, ny, nz, dtype)
+    m, f, y = setup(pw, nx, ny, nz, dtype, algo=algo)
     c = oracle.Coeffs(nz, 50.0, 30.0)
     y_eff = [y[0], y[1], y[2].copy()]
     y_eff[2][:, :, -1] = 0.0
@@ -66,9 +69,10 @@ def test_adjoint_matches_oracle(pw, shape, dtype):
     assert not h[:2].any() and not h[:, :2].any()
 
 
-def test_alpha_beta(pw):
+@pytest.mark.parametrize("algo", ["native", "split"])
+def test_alpha_beta(pw, algo):
     nx, ny, nz = 16, 12, 9
-    m, f, y = setup(pw, nx, ny, nz, "f64")
+    m, f, y = setup(pw, nx, ny, nz, "f64", algo=algo)
     base, _ = gpu_adjoint(m, f, y)
     rng = np.random.default_rng(9)
     init = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
@@ -77,10 +81,11 @@ def test_alpha_beta(pw):
         np.testing.assert_allclose(got[q], init[q] - 2.5 * base[q], rtol=1e-13, atol=1e-13)
 
 
-def test_euler_adjoint(pw):
+@pytest.mark.parametrize("algo", ["native", "split"])
+def test_euler_adjoint(pw, algo):
     nx, ny, nz = 18, 14, 10
     dt = 0.5
-    m, f, y = setup(pw, nx, ny, nz, "f64")
+    m, f, y = setup(pw, nx, ny, nz, "f64", algo=algo)
     base, _ = gpu_adjoint(m, f, y)
     U = [m.from_interior(a) for a in f]
     Y = [m.from_interior(a, fill_halo=False) for a in y]
@@ -94,11 +99,12 @@ def test_euler_adjoint(pw):
         np.testing.assert_allclose(m.interior(G[q]).double().cpu().numpy(), want, rtol=1e-13, atol=1e-13)
 
 
-def test_dot_product_identity_on_device(pw):
+@pytest.mark.parametrize("algo", ["native", "split"])
+def test_dot_product_identity_on_device(pw, algo):
     """<J e, y> = <e, J^T y> with J e from the GPU forward by central differences
     (exact up to rounding: the sources are quadratic)."""
     nx, ny, nz = 20, 16, 12
-    m, f, y = setup(pw, nx, ny, nz, "f64")
+    m, f, y = setup(pw, nx, ny, nz, "f64", algo=algo)
     rng = np.random.default_rng(5)
     e = [rng.standard_normal((nx, ny, nz)) for _ in range(3)]
     e[2][:, :, -1] = 0.0
@@ -117,3 +123,20 @@ def test_dot_product_identity_on_device(pw):
     rhs = sum(float(np.sum(e[q] * JTy[q])) for q in range(3))
     scale = sum(float(np.sum(np.abs(Je[q] * y[q]))) for q in range(3))
     assert abs(lhs - rhs) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("kind", ["huge", "nan"])
+def test_split_adjoint_out_of_range_is_reported(pw, kind):
+    """The double-float adjoint reports inputs outside its range (here an
+    incoming gradient) as PW_ERR_RANGE, like the forward."""
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz = 14, 12, 10
+    m, f, y = setup(pw, nx, ny, nz, "f64", algo="split")
+    y[1][5, 6, 3] = 2.0 ** 41 if kind == "huge" else np.nan
+    U = [m.from_interior(a) for a in f]
+    Y = [m.from_interior(a, fill_halo=False) for a in y]
+    G = [m.zeros() for _ in range(3)]
+    m.adjoint(*U, *Y, *G)
+    torch.cuda.synchronize()
+    assert m.device_status() == L.PW_ERR_RANGE
+    assert m.device_status() == 0

@@ -125,9 +125,9 @@ def test_fused_steps_stay_in_their_fields(pw, shape, dtype, algo):
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_adjoint_euler_and_sums_stay_in_their_fields(pw, shape, dtype):
-    m = pw.Mesh(*shape, 45.0, 35.0, dtype=dtype, algo="native")
+@pytest.mark.parametrize("dtype,algo", [("f64", "native"), ("f64", "split"), ("f32", "auto")])
+def test_adjoint_euler_and_sums_stay_in_their_fields(pw, shape, dtype, algo):
+    m = pw.Mesh(*shape, 45.0, 35.0, dtype=dtype, algo=algo)
     U = fields(pw, m, 505)
     Y = fields(pw, m, 506)
     su, sy = snapshot(U), snapshot(Y)
