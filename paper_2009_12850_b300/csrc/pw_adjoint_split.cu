@@ -26,8 +26,11 @@ struct PwAdjSplitGeom {
     double tcx, tcy;
 };
 
-#define PW_ASPLIT_RAW 2
-#define PW_ASPLIT_CONV 4
+// one raw TMA slot and three converted planes (i-1, i, i+1): 72 KB, so three
+// CTAs share an SM; converting into the slot of plane i-2 needs a barrier after
+// the previous step, and the raw slot is refilled after a second barrier
+#define PW_ASPLIT_RAW 1
+#define PW_ASPLIT_CONV 3
 
 __device__ __forceinline__ D2 pw_ald(const float4 *p, int q) {
     const float4 c = p[q];
@@ -41,7 +44,7 @@ __device__ __forceinline__ float2 pw_coef_pair(double c) {
 }
 
 template <int TJ, int KC>
-__global__ void __launch_bounds__(TJ *(KC > 0 ? KC / 2 : (TJ == 4 ? 32 : 16)), 2)
+__global__ void __launch_bounds__(TJ *(KC > 0 ? KC / 2 : (TJ == 4 ? 32 : 16)), 3)
 pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                         const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap my,
                         const __grid_constant__ CUtensorMap mz, const __grid_constant__ CUtensorMap mq,
@@ -163,12 +166,15 @@ pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_con
     auto L = [&](const float4 *B, int f, int o, int sh) { return pw_ald(B, f * cfs + o * cw + sh); };
 
     for (int p = 0; p < nplanes; p++) {
+        // the raw plane p has landed and every thread is past step p-1 (its
+        // converted slot, that of plane p-3, is free)
         const bool ok = pw_mbar_wait_bounded(&bars[p % PW_ASPLIT_RAW], (uint32_t)((p / PW_ASPLIT_RAW) & 1));
-        if (ok) convert(p);
         if (!__syncthreads_and(ok)) {
             give_up(p);
             return;
         }
+        convert(p);
+        __syncthreads();  // plane p converted; the raw slot takes plane p + 1
         if (tid == 0 && p + PW_ASPLIT_RAW < nplanes) {
             issue(p + PW_ASPLIT_RAW);
             issued = p + PW_ASPLIT_RAW + 1;

@@ -24,11 +24,10 @@
 // barrier the raw slot is refilled (two planes of look-ahead) and the threads
 // compute column i from converted planes i-1, i, i+1.
 //
-// The algebra is the PW form regrouped around the face coefficients:
-//   tzc1(k) = g(k-1) r(k), tzc2(k) = g(k) r(k),   g = 0.25 rho_w, r = 1/(rho_n dz)
-//   tzd1(k) = g'(k) r'(k), tzd2(k) = g'(k+1) r'(k), g' = 0.25 rho_n, r' = 1/(rho_w dzn)
-// so that  s = tcx X + tcy Y + r Z  with X, Y, Z differences of products of a
-// field value and an (unscaled, or g-scaled for the vertical) face sum.
+// The algebra: s = tcx X + tcy Y + Z with X, Y differences of products of a
+// field value and a face sum, and Z = phi(k-1) (A(k-1) c1) - phi(k+1) (A(k) c2)
+// with the vertical coefficients c1, c2 (tzc1, tzc2 or tzd1, tzd2) applied to
+// the face sums A; when tcx == tcy (a square horizontal grid) s = tcx (X + Y) + Z.
 #include <algorithm>
 
 #include "pw_df.cuh"
@@ -43,8 +42,8 @@ struct PwSplitGeom {
     int ti;            // columns marched per CTA
     int rfs;           // doubles between the u, v, w planes of a raw slot (128-byte aligned)
     int cfs;           // 16-byte chunks between the u, v, w planes of a converted slot
-    int cs_n;          // levels in the coefficient table (nz + 4, level -2 first)
     long long si, sj;
+    double tcx, tcy;
 };
 
 #define PW_SPLIT_RAW 2   // raw TMA slots
@@ -58,12 +57,12 @@ __device__ __forceinline__ D2 pw_ldc(const float4 *row, int q) {
 
 // STEP: write x + dt S(x) (x read exactly from xu, xv, xw) to su, sv, sw and to
 // their periodic halo images, the forward Euler step fused into the stencil
-template <int TJ, int KC, bool BETA, bool STEP = false>
+template <int TJ, int KC, bool BETA, bool STEP = false, bool ISO = false>
 __global__ void __launch_bounds__(128, 4)
 pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                        const __grid_constant__ CUtensorMap mw, double *__restrict__ su,
                        double *__restrict__ sv, double *__restrict__ sw,
-                       const float *__restrict__ cs, const PwSplitGeom g,
+                       const double *__restrict__ cz, const PwSplitGeom g,
                        int *__restrict__ status, const double *__restrict__ xu = nullptr,
                        const double *__restrict__ xv = nullptr, const double *__restrict__ xw = nullptr,
                        double dt = 0.0) {
@@ -168,26 +167,27 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
 
     // coefficients of this thread's level pair, prepared once per CTA in shared
     // memory (keeps them out of the register file during the march): per
-    // thread column tk: Gm, G0, GP0, GPp, R0, RP0 as float4 (hi pair, lo pair)
-    auto tab = [&](int arr, int k, bool hi) {
-        const int kq = min(k, g.nz + 1);  // the table covers levels -2 .. nz+1 (0 outside the grid)
-        return cs[(2 * arr + (hi ? 0 : 1)) * g.cs_n + kq + 2];
+    // thread column tk: tzc1, tzc2, tzd1, tzd2 of levels (ka, kz) as float4
+    // (hi pair, lo pair), split from the FP64 table; then tcx, tcy
+    auto cpair = [](double c) {
+        const float h = (float)c;
+        return make_float2(h, (float)(c - (double)h));
     };
     for (int t = tid; t < half; t += nt) {
         const int a = k0 + t, b = a + half;
-        const int arrs[6] = {0, 0, 1, 1, 2, 3};
-        const int offs[6] = {-1, 0, 0, 1, 0, 0};
-        for (int c = 0; c < 6; c++)
-            ctab[t * 6 + c] = make_float4(tab(arrs[c], a + offs[c], true), tab(arrs[c], b + offs[c], true),
-                                          tab(arrs[c], a + offs[c], false), tab(arrs[c], b + offs[c], false));
+        for (int c = 0; c < 4; c++) {
+            const float2 x = cpair(a < g.nz ? cz[c * g.nz + a] : 0.0);
+            const float2 y = cpair(b < g.nz ? cz[c * g.nz + b] : 0.0);
+            ctab[t * 4 + c] = make_float4(x.x, y.x, x.y, y.y);
+        }
     }
     if (tid == 0) {
-        const float *tc = cs + 8 * g.cs_n;
-        ctab[half * 6] = make_float4(tc[0], tc[0], tc[1], tc[1]);
-        ctab[half * 6 + 1] = make_float4(tc[2], tc[2], tc[3], tc[3]);
+        const float2 x = cpair(g.tcx), y = cpair(g.tcy);
+        ctab[half * 4] = make_float4(x.x, x.x, x.y, x.y);
+        ctab[half * 4 + 1] = make_float4(y.x, y.x, y.y, y.y);
     }
-    auto coef = [&](int a) { return pw_ldc(ctab, tk * 6 + a); };
-    auto tcoef = [&](int a) { return pw_ldc(ctab, half * 6 + a); };
+    auto coef = [&](int a) { return pw_ldc(ctab, tk * 4 + a); };
+    auto tcoef = [&](int a) { return pw_ldc(ctab, half * 4 + a); };
     const bool active = j < g.ny;
     const bool oka = ka < g.nz, okz = kz < g.nz;
 
@@ -197,6 +197,12 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     auto base = [&](int p) { return conv + (size_t)(p % PW_SPLIT_CONV) * 3 * cfs + tb; };
     auto L = [&](const float4 *B, int f, int o, int sh) { return pw_ldc(B, f * cfs + o * cw + sh); };
 
+    // tcx X + tcy Y + Z; with tcx == tcy (a square horizontal grid) one product
+    // (the table is read after the first barrier of the march)
+    auto horiz = [&](D2 X, D2 Y, D2 Z) {
+        if constexpr (ISO) return df_add(df_mul(df_add(X, Y), tcoef(0)), Z);
+        else return df_add(df_add(df_mul(X, tcoef(0)), df_mul(Y, tcoef(1))), Z);
+    };
     D2 Fx_m, Gx_m, Hx_m;  // x face sums of column i-1|i, carried along the march
     for (int p = 0; p < nplanes; p++) {
         const bool ok = pw_mbar_wait_bounded(&bars[p % PW_SPLIT_RAW], (uint32_t)((p / PW_SPLIT_RAW) & 1));
@@ -224,40 +230,37 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
         // ---------------- su ----------------
         const D2 uM0 = L(BM, 0, 1, 0), uC0 = L(BC, 0, 1, 0), uP0 = L(BP, 0, 1, 0);
         const D2 Fx_p = df_add(uC0, uP0);
-        D2 X = df_mul(df_sub(df_mul(uM0, Fx_m), df_mul(uP0, Fx_p)), tcoef(0));
+        D2 X = df_sub(df_mul(uM0, Fx_m), df_mul(uP0, Fx_p));
         const D2 uS0 = L(BC, 0, 0, 0), uN0 = L(BC, 0, 2, 0);
         const D2 vS0 = L(BC, 1, 0, 0), vSP0 = L(BP, 1, 0, 0);
         const D2 vC0 = L(BC, 1, 1, 0), vP0 = L(BP, 1, 1, 0);
-        D2 Y = df_mul(df_sub(df_mul(uS0, df_add(vS0, vSP0)), df_mul(uN0, df_add(vC0, vP0))), tcoef(1));
+        D2 Y = df_sub(df_mul(uS0, df_add(vS0, vSP0)), df_mul(uN0, df_add(vC0, vP0)));
         const D2 wCm = L(BC, 2, 1, -1), wPm = L(BP, 2, 1, -1);
         const D2 wC0 = L(BC, 2, 1, 0), wP0 = L(BP, 2, 1, 0);
         const D2 uCm = L(BC, 0, 1, -1), uCp = L(BC, 0, 1, 1);
-        D2 Z = df_mul(df_sub(df_mul(uCm, df_mul(df_add(wCm, wPm), coef(0))),
-                             df_mul(uCp, df_mul(df_add(wC0, wP0), coef(1)))), coef(4));
-        const D2 ru = df_add(df_add(X, Y), Z);
+        D2 Z = df_sub(df_mul(uCm, df_mul(df_add(wCm, wPm), coef(0))), df_mul(uCp, df_mul(df_add(wC0, wP0), coef(1))));
+        const D2 ru = horiz(X, Y, Z);
 
         // ---------------- sv ----------------
         const D2 vM0 = L(BM, 1, 1, 0);
         const D2 Gx_p = df_add(uC0, uN0);
-        X = df_mul(df_sub(df_mul(vM0, Gx_m), df_mul(vP0, Gx_p)), tcoef(0));
+        X = df_sub(df_mul(vM0, Gx_m), df_mul(vP0, Gx_p));
         const D2 vN0 = L(BC, 1, 2, 0);
-        Y = df_mul(df_sub(df_mul(vS0, df_add(vS0, vC0)), df_mul(vN0, df_add(vC0, vN0))), tcoef(1));
+        Y = df_sub(df_mul(vS0, df_add(vS0, vC0)), df_mul(vN0, df_add(vC0, vN0)));
         const D2 wNm = L(BC, 2, 2, -1), wN0 = L(BC, 2, 2, 0);
         const D2 vCm = L(BC, 1, 1, -1), vCp = L(BC, 1, 1, 1);
-        Z = df_mul(df_sub(df_mul(vCm, df_mul(df_add(wCm, wNm), coef(0))),
-                          df_mul(vCp, df_mul(df_add(wC0, wN0), coef(1)))), coef(4));
-        const D2 rv = df_add(df_add(X, Y), Z);
+        Z = df_sub(df_mul(vCm, df_mul(df_add(wCm, wNm), coef(0))), df_mul(vCp, df_mul(df_add(wC0, wN0), coef(1))));
+        const D2 rv = horiz(X, Y, Z);
 
         // ---------------- sw ----------------
         const D2 wM0 = L(BM, 2, 1, 0);
         const D2 Hx_p = df_add(uC0, uCp);
-        X = df_mul(df_sub(df_mul(wM0, Hx_m), df_mul(wP0, Hx_p)), tcoef(0));
+        X = df_sub(df_mul(wM0, Hx_m), df_mul(wP0, Hx_p));
         const D2 wS0 = L(BC, 2, 0, 0), vSp = L(BC, 1, 0, 1);
-        Y = df_mul(df_sub(df_mul(wS0, df_add(vS0, vSp)), df_mul(wN0, df_add(vC0, vCp))), tcoef(1));
+        Y = df_sub(df_mul(wS0, df_add(vS0, vSp)), df_mul(wN0, df_add(vC0, vCp)));
         const D2 wCp = L(BC, 2, 1, 1);
-        Z = df_mul(df_sub(df_mul(wCm, df_mul(df_add(wCm, wC0), coef(2))),
-                          df_mul(wCp, df_mul(df_add(wC0, wCp), coef(3)))), coef(5));
-        const D2 rw = df_add(df_add(X, Y), Z);
+        Z = df_sub(df_mul(wCm, df_mul(df_add(wCm, wC0), coef(2))), df_mul(wCp, df_mul(df_add(wC0, wCp), coef(3))));
+        const D2 rw = horiz(X, Y, Z);
 
         Fx_m = Fx_p;
         Gx_m = Gx_p;
@@ -329,14 +332,15 @@ static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v,
     g.ti = tile_i;
     g.rfs = ((tile_j + 2) * g.kb + 15) / 16 * 16;  // 128-byte aligned TMA destinations
     g.cfs = (tile_j + 2) * g.cw;
-    g.cs_n = m->nz + 4;
     g.si = m->si;
     g.sj = m->sj;
+    g.tcx = m->tcx;
+    g.tcy = m->tcy;
     const int threads = g.half * tile_j;
     if (threads > 128)
         return pw_fail(PW_ERR_SHAPE, "split kernel: tile_j=%d needs %d threads (max 128)", tile_j, threads);
     const size_t smem = (size_t)PW_SPLIT_RAW * 3 * g.rfs * 8 + (size_t)PW_SPLIT_CONV * 3 * g.cfs * 16 + 64 +
-                        ((size_t)g.half * 6 + 2) * sizeof(float4);
+                        ((size_t)g.half * 4 + 2) * sizeof(float4);
     if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "split kernel needs %zu bytes of shared memory", smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
@@ -350,21 +354,20 @@ static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v,
     const bool full = g.kc == kc_max;
     using KernT = decltype(&pw_advect_split_kernel<8, 32, false, false>);
     KernT kern;
-    if (tile_j == 8) {
-        if (step) kern = full ? pw_advect_split_kernel<8, 32, false, true> : pw_advect_split_kernel<8, 0, false, true>;
-        else if (beta) kern = full ? pw_advect_split_kernel<8, 32, true> : pw_advect_split_kernel<8, 0, true>;
-        else kern = full ? pw_advect_split_kernel<8, 32, false> : pw_advect_split_kernel<8, 0, false>;
-    } else {
-        if (step) kern = full ? pw_advect_split_kernel<4, 64, false, true> : pw_advect_split_kernel<4, 0, false, true>;
-        else if (beta) kern = full ? pw_advect_split_kernel<4, 64, true> : pw_advect_split_kernel<4, 0, true>;
-        else kern = full ? pw_advect_split_kernel<4, 64, false> : pw_advect_split_kernel<4, 0, false>;
-    }
+    const bool iso = m->tcx == m->tcy;
+#define PW_SPLIT_PICK(TJ, KC)                                                                        \
+    (step ? (iso ? pw_advect_split_kernel<TJ, KC, false, true, true> : pw_advect_split_kernel<TJ, KC, false, true>) \
+     : beta ? (iso ? pw_advect_split_kernel<TJ, KC, true, false, true> : pw_advect_split_kernel<TJ, KC, true>)     \
+            : (iso ? pw_advect_split_kernel<TJ, KC, false, false, true> : pw_advect_split_kernel<TJ, KC, false>))
+    if (tile_j == 8) kern = full ? PW_SPLIT_PICK(8, 32) : PW_SPLIT_PICK(8, 0);
+    else kern = full ? PW_SPLIT_PICK(4, 64) : PW_SPLIT_PICK(4, 0);
+#undef PW_SPLIT_PICK
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((m->nz + g.kc - 1) / g.kc), (unsigned)((m->ny + tile_j - 1) / tile_j),
               (unsigned)((m->nx + tile_i - 1) / tile_i));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_j or tile_i");
     kern<<<grid, threads, smem, st>>>(maps[0], maps[1], maps[2], (double *)su, (double *)sv, (double *)sw,
-                                      m->coefsplit, g, m->status, (const double *)u, (const double *)v,
+                                      m->coef64 + 6 * m->nz, g, m->status, (const double *)u, (const double *)v,
                                       (const double *)w, dt);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
