@@ -43,7 +43,7 @@ __device__ __forceinline__ float2 pw_coef_pair(double c) {
     return make_float2(h, (float)(c - (double)h));
 }
 
-template <int TJ, int KC>
+template <int TJ, int KC, bool ISO>
 __global__ void __launch_bounds__(TJ *(KC > 0 ? KC / 2 : (TJ == 4 ? 32 : 16)), 3)
 pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                         const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap my,
@@ -183,6 +183,11 @@ pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_con
         const int i = i0 + p - 2;
         const float4 *BM = base(p - 2), *BC = base(p - 1), *BP = base(p);
         const D2 tcx = pw_ald(ctab, half * 7), tcy = pw_ald(ctab, half * 7 + 1);
+        // tcx X + tcy Y + Z; with tcx == tcy (a square horizontal grid) one product
+        auto horiz = [&](D2 X, D2 Y, D2 Z) {
+            if constexpr (ISO) return df_add(df_mul(tcx, df_add(X, Y)), Z);
+            else return df_add(df_add(df_mul(tcx, X), df_mul(tcy, Y)), Z);
+        };
         const float4 *ct = ctab + tk * 7;
         const D2 C1p = pw_ald(ct, 0), C2m = pw_ald(ct, 1), C2 = pw_ald(ct, 2);
         const D2 D1p = pw_ald(ct, 3), D1 = pw_ald(ct, 4), Dd2 = pw_ald(ct, 5), D2m = pw_ald(ct, 6);
@@ -205,7 +210,7 @@ pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_con
             X = df_add(X, df_sub(df_add(df_mul(qp, w0), df_mul(qpm, w0m)), df_add(df_mul(q0, wp), df_mul(q0m, wpm))));
             const D2 Yt = df_sub(df_mul(yn, df_add(v0, vp)), df_mul(ys, df_add(vs, vsp)));
             const D2 Zt = df_sub(df_mul(df_mul(C1p, y0p), df_add(w0, wp)), df_mul(df_mul(C2m, y0m), df_add(w0m, wpm)));
-            ru = df_add(df_add(df_mul(tcx, X), df_mul(tcy, Yt)), Zt);
+            ru = horiz(X, Yt, Zt);
         }
         // ---------------- gv ----------------
         D2 rv;
@@ -224,7 +229,7 @@ pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_con
             Yt = df_add(Yt, df_sub(df_mul(v0, df_sub(zn, zs)), df_mul(z0, df_sub(vn, vs))));
             Yt = df_add(Yt, df_sub(df_add(df_mul(qn, w0), df_mul(qnm, w0m)), df_add(df_mul(q0, wn), df_mul(q0m, wnm))));
             const D2 Zt = df_sub(df_mul(df_mul(C1p, z0p), df_add(w0, wn)), df_mul(df_mul(C2m, z0m), df_add(w0m, wnm)));
-            rv = df_add(df_add(df_mul(tcx, Xt), df_mul(tcy, Yt)), Zt);
+            rv = horiz(Xt, Yt, Zt);
         }
         // ---------------- gw ----------------
         D2 rw;
@@ -246,7 +251,7 @@ pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_con
             Zt = df_sub(Zt, df_mul(C2, df_add(df_mul(z0, v0p), df_mul(zs, vsp))));
             Zt = df_add(Zt, df_add(df_mul(df_mul(D1p, q0p), w0), df_mul(df_mul(D1, q0), w0m)));
             Zt = df_sub(Zt, df_add(df_mul(df_mul(Dd2, q0), w0p), df_mul(df_mul(D2m, q0m), w0)));
-            rw = df_add(df_add(df_mul(tcx, Xt), df_mul(tcy, Yt)), Zt);
+            rw = horiz(Xt, Yt, Zt);
         }
         if (!active) continue;
 
@@ -302,7 +307,9 @@ pw_status pw_launch_adjoint_split(const pw_mesh *m, const void *const *in, void 
                                         tile_j + 2);
         if (s != PW_OK) return s;
     }
-    auto kern = g.kc == kc_max ? pw_adjoint_split_kernel<8, 32> : pw_adjoint_split_kernel<8, 0>;
+    const bool iso = m->tcx == m->tcy;
+    auto kern = g.kc == kc_max ? (iso ? pw_adjoint_split_kernel<8, 32, true> : pw_adjoint_split_kernel<8, 32, false>)
+                               : (iso ? pw_adjoint_split_kernel<8, 0, true> : pw_adjoint_split_kernel<8, 0, false>);
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((m->nz + g.kc - 1) / g.kc), (unsigned)((m->ny + tile_j - 1) / tile_j),
               (unsigned)((m->nx + g.ti - 1) / g.ti));
