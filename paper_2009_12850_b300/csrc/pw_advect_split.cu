@@ -17,12 +17,14 @@
 //
 // Pipeline per x step: TMA brings the (j,k) plane of u, v, w (doubles, rows
 // j0-1 .. j0+TJ, levels k0-2 .. k0+KC+1; levels >= nz and the w lid arrive as
-// zeros because the tensor maps carry the logical k extent) into one of two
-// raw slots; all threads convert it, with integer bit operations, into a ring
-// of four converted planes whose 16-byte chunk q of a row holds
-// (hi, hi, lo, lo) of levels (k0 + q - 1, k0 + q - 1 + KC/2); after a CTA
-// barrier the raw slot is refilled (two planes of look-ahead) and the threads
-// compute column i from converted planes i-1, i, i+1.
+// zeros because the tensor maps carry the logical k extent) into the raw slot;
+// after a barrier (the oldest converted plane is no longer read) all threads
+// convert it, with integer bit operations, into a ring of three converted
+// planes whose 16-byte chunk q of a row holds (hi, hi, lo, lo) of levels
+// (k0 + q - 1, k0 + q - 1 + KC/2); after a second barrier the raw slot takes
+// the next plane (its copy runs during the arithmetic) and the threads compute
+// column i from converted planes i-1, i, i+1.  One raw slot and three
+// converted planes (35 KB for the 8 x 32 tile) let five CTAs share an SM.
 //
 // The algebra: s = tcx X + tcy Y + Z with X, Y differences of products of a
 // field value and a face sum, and Z = phi(k-1) (A(k-1) c1) - phi(k+1) (A(k) c2)
@@ -46,8 +48,8 @@ struct PwSplitGeom {
     double tcx, tcy;
 };
 
-#define PW_SPLIT_RAW 2   // raw TMA slots
-#define PW_SPLIT_CONV 4  // converted planes (i-1, i, i+1 in use, i+2 being written)
+#define PW_SPLIT_RAW 1   // raw TMA slots
+#define PW_SPLIT_CONV 3  // converted planes (i-1, i, i+1)
 
 // one level pair (a, b) of a converted row as hi and lo pairs
 __device__ __forceinline__ D2 pw_ldc(const float4 *row, int q) {
@@ -58,7 +60,7 @@ __device__ __forceinline__ D2 pw_ldc(const float4 *row, int q) {
 // STEP: write x + dt S(x) (x read exactly from xu, xv, xw) to su, sv, sw and to
 // their periodic halo images, the forward Euler step fused into the stencil
 template <int TJ, int KC, bool BETA, bool STEP = false, bool ISO = false>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 5)
 pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
                        const __grid_constant__ CUtensorMap mw, double *__restrict__ su,
                        double *__restrict__ sv, double *__restrict__ sw,
@@ -143,6 +145,16 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
         soff[m] = src_of(R, tk + 1);
         doff[m] = R * cw + tk + 1;
     }
+    // this thread's edge chunk (fixed tiles): 8 x 32: warp 3 (rows 6, 7: three
+    // main rows each) takes edges 0-31, warps 0-2 share the other 28;
+    // 4 x 64: warps 2, 3 (four main rows) take the 36 edges
+    int edge = -1;
+    if constexpr (CT) {
+        const int warp = tid >> 5, lane = tid & 31;
+        if (TJ == 8) edge = warp == 3 ? lane : (lane * 3 + warp < 2 * ROWS - 32 ? 32 + lane * 3 + warp : -1);
+        else edge = warp >= 2 && (warp - 2) * 32 + lane < 2 * ROWS ? (warp - 2) * 32 + lane : -1;
+    }
+    const int esrc = edge >= 0 ? src_of(edge >> 1, (edge & 1) ? cw - 1 : 0) : 0;
     auto conv_one = [&](const double *rs, float4 *cd, int so, int dof) {
         const uint2 a = *reinterpret_cast<const uint2 *>(rs + so);
         const uint2 b = *reinterpret_cast<const uint2 *>(rs + so + half);
@@ -157,10 +169,19 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
 #pragma unroll
         for (int m = 0; m < MR; m++)
             if (m + 1 < MR || tj + m * TJ < ROWS) conv_one(rs, cd, soff[m], doff[m]);
-        // the two edge chunks of each row (q = 0 and q = cw-1)
-        for (int e = tid; e < 2 * ROWS; e += nt) {
-            const int R = e >> 1, q = (e & 1) ? cw - 1 : 0;
-            conv_one(rs, cd, src_of(R, q), R * cw + q);
+        // the two edge chunks of each row (q = 0 and q = cw-1): for the fixed
+        // tiles, handed first to the warps with fewer main rows (so that every
+        // warp reaches the barrier with about the same work)
+        if constexpr (CT) {
+            if (edge >= 0) {
+                const int R = edge >> 1, q = (edge & 1) ? cw - 1 : 0;
+                conv_one(rs, cd, esrc, R * cw + q);
+            }
+        } else {
+            for (int e = tid; e < 2 * ROWS; e += nt) {
+                const int R = e >> 1, q = (e & 1) ? cw - 1 : 0;
+                conv_one(rs, cd, src_of(R, q), R * cw + q);
+            }
         }
         pw_fence_proxy_async();  // these reads come before the TMA refill of the slot
     };
@@ -206,11 +227,12 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     D2 Fx_m, Gx_m, Hx_m;  // x face sums of column i-1|i, carried along the march
     for (int p = 0; p < nplanes; p++) {
         const bool ok = pw_mbar_wait_bounded(&bars[p % PW_SPLIT_RAW], (uint32_t)((p / PW_SPLIT_RAW) & 1));
-        if (ok) convert(p);
         if (!__syncthreads_and(ok)) {
             give_up(p);
             return;
         }
+        convert(p);
+        __syncthreads();
         // every thread has converted plane p: its raw slot takes plane p + 2
         if (tid == 0 && p + PW_SPLIT_RAW < nplanes) {
             issue(p + PW_SPLIT_RAW);
