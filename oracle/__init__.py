@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of the Piacsek-Williams advection source terms.
+"""FP64 CPU oracle of the Piacsek-Williams advection source terms (and of the
+ULTIMATE-QUICKEST scalar scheme the paper names beside it).
 
 TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and the CPU legs of
 bench.py may import this package; the library and its Python binding never do.
@@ -55,6 +56,13 @@ def lib():
         L.pwo_scalar_points.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_D] * 2 + [_D] * 4
                                         + [ctypes.c_long, _L, _D, _D])
         L.pwo_scalar_points.restype = None
+        L.pwo_tvd_coeffs.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D]
+        L.pwo_tvd_coeffs.restype = None
+        L.pwo_tvd_src.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_D] * 3 + [_D] * 4 + [_D, _D]
+        L.pwo_tvd_src.restype = None
+        L.pwo_tvd_points.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_D] * 3 + [_D] * 4
+                                     + [ctypes.c_long, _L, _D, _D])
+        L.pwo_tvd_points.restype = None
         _lib = L
     return _lib
 
@@ -124,6 +132,9 @@ class Coeffs:
                                 _p(self.hz1), _p(self.hz2))
         self.hx = 0.5 / self.dx
         self.hy = 0.5 / self.dy
+        # flux-form vertical coefficients of the ULTIMATE-QUICKEST scheme
+        self.fz1, self.fz2 = np.zeros(self.nz), np.zeros(self.nz)
+        lib().pwo_tvd_coeffs(self.nz, _p(self.dz), _p(self.rho_n), _p(self.rho_w), _p(self.fz1), _p(self.fz2))
 
     def args(self):
         return (self.tcx, self.tcy, _p(self.tzc1), _p(self.tzc2), _p(self.tzd1), _p(self.tzd2))
@@ -213,6 +224,32 @@ def scalar_points(c: Coeffs, u, v, w, phi, pts):
     cond = np.empty(n)
     lib().pwo_scalar_points(nx, ny, nz, c.hx, c.hy, _p(c.hz1), _p(c.hz2), _p(u), _p(v), _p(w), _p(phi), n,
                             pts.ctypes.data_as(_L), _p(out), _p(cond))
+    return out, cond
+
+
+def advect_tvd(c: Coeffs, u, v, w, phi, dt, want_cond=False):
+    """ULTIMATE-QUICKEST flux-form source of the scalar phi advected by
+    (u, v, w) over one step dt (and its per-point condition sums if asked)."""
+    u, v, w, phi = _f64(u), _f64(v), _f64(w), _f64(phi)
+    nx, ny, nz = _shape(u)
+    assert nz == c.nz and phi.shape == u.shape
+    out = np.empty_like(u)
+    cond = np.empty_like(u) if want_cond else None
+    lib().pwo_tvd_src(nx, ny, nz, c.dx, c.dy, float(dt), _p(c.dz), _p(c.fz1), _p(c.fz2),
+                      _p(u), _p(v), _p(w), _p(phi), _p(out), _p(cond))
+    return (out, cond) if want_cond else out
+
+
+def tvd_points(c: Coeffs, u, v, w, phi, dt, pts):
+    """ULTIMATE-QUICKEST source at the given (n, 3) integer points; returns (values, cond)."""
+    u, v, w, phi = _f64(u), _f64(v), _f64(w), _f64(phi)
+    nx, ny, nz = _shape(u)
+    pts = np.ascontiguousarray(pts, dtype=np.int64)
+    n = pts.shape[0]
+    out = np.empty(n)
+    cond = np.empty(n)
+    lib().pwo_tvd_points(nx, ny, nz, c.dx, c.dy, float(dt), _p(c.dz), _p(c.fz1), _p(c.fz2),
+                         _p(u), _p(v), _p(w), _p(phi), n, pts.ctypes.data_as(_L), _p(out), _p(cond))
     return out, cond
 
 

@@ -587,12 +587,196 @@ def pin_adjoint_cond():
     assert abs(g1[0][i, j, k]) < c1[0][i, j, k] * (1 - 1e-6)      # contributions of both signs
 
 
+
+# --------------------------------------------------------------------------
+# pins of the ULTIMATE-QUICKEST scalar scheme (section 3.1's second scheme)
+# --------------------------------------------------------------------------
+def tvd_column_coeffs(dz):
+    n = len(dz)
+    return oracle.Coeffs(n, 1.0, 1.0, dz=np.asarray(dz, float), rho_n=np.ones(n), rho_w=np.ones(n), rho0=1.0)
+
+
+def pin_tvd_worked_examples():
+    spec = json.load(open(os.path.join(GOLDEN, "tvd_worked_examples.json")))
+    c = tvd_column_coeffs(spec["grid"]["dz"])
+    z = np.zeros((1, 1, 4))
+    for e in spec["examples"]:
+        w = np.array(e["w"]).reshape(1, 1, 4)
+        phi = np.array(e["phi"]).reshape(1, 1, 4)
+        s = oracle.advect_tvd(c, z + 3.0, z - 2.0, w, phi, e["dt"])[0, 0]
+        np.testing.assert_allclose(s, e["expect"], rtol=0, atol=1e-14, err_msg=e["name"])
+
+
+def pin_tvd_coefficients_and_constants():
+    # fz1, fz2 are the doubled scalar PW coefficients with the ground and lid faces dropped
+    c = stretched(9)
+    np.testing.assert_allclose(c.fz1[1:], 2 * c.hz1[1:], rtol=1e-15)
+    np.testing.assert_allclose(c.fz2[:-1], 2 * c.hz2[:-1], rtol=1e-15)
+    assert c.fz1[0] == 0.0 and c.fz2[-1] == 0.0
+    # a constant field: every face carries the constant, so s = C * (inflow - outflow)
+    rng = np.random.default_rng(31)
+    nx, ny, nz = 6, 5, 9
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    u, v = u - 5 + 2 * rng.standard_normal(u.shape), v - 5 + 2 * rng.standard_normal(v.shape)
+    C = 2.75
+    s = oracle.advect_tvd(c, u, v, w, np.full((nx, ny, nz), C), dt=3.0)
+    wb = np.concatenate([np.zeros((nx, ny, 1)), w[:, :, :-1]], axis=2)   # w(k-1), ground 0
+    wt = w.copy()
+    wt[:, :, -1] = 0.0                                                     # lid
+    div = ((np.roll(u, 1, 0) - u) / c.dx + (np.roll(v, 1, 1) - v) / c.dy
+           + c.fz1[None, None, :] * wb - c.fz2[None, None, :] * wt)
+    np.testing.assert_allclose(s, C * div, rtol=1e-13, atol=1e-13 * np.abs(C * div).max())
+
+
+def pin_tvd_courant_one_shift():
+    rng = np.random.default_rng(32)
+    # x and y: uniform flow of Courant number 1 moves every cell one cell on
+    for axis, (nx, ny) in ((0, (11, 3)), (1, (3, 13))):
+        c = oracle.Coeffs(2, 40.0, 25.0)
+        h = c.dx if axis == 0 else c.dy
+        phi = rng.random((nx, ny, 2)) * 10 - 3
+        for U in (7.0, -7.0):
+            wind = [np.zeros((nx, ny, 2)) for _ in range(3)]
+            wind[axis][:] = U
+            dt = h / abs(U)
+            new = phi + dt * oracle.advect_tvd(c, *wind, phi, dt)
+            np.testing.assert_allclose(new, np.roll(phi, 1 if U > 0 else -1, axis), rtol=0, atol=1e-13)
+            # above Courant number 1 the limiter's window [t_C, t_C / c] is empty
+            # and closes on its lower end: every face takes the upwind value
+            dt = 1.6 * h / abs(U)
+            up = np.roll(phi, 1, axis) if U > 0 else np.roll(phi, -1, axis)
+            new = phi + dt * oracle.advect_tvd(c, *wind, phi, dt)
+            np.testing.assert_allclose(new, phi - 1.6 * (phi - up), rtol=0, atol=1e-13)
+    # z on a stretched column of unit density: w(k) = dz(C)/dt makes every
+    # interior face Courant 1, so each cell's content dz(k) phi(k) moves one cell
+    dz = np.array([3.0, 5.0, 2.0, 7.0, 4.0, 6.0, 1.5])
+    nz = len(dz)
+    c = tvd_column_coeffs(dz)
+    phi = rng.random((2, 1, nz)) + 0.5
+    M = dz * phi
+    dt = 0.25
+    for up in (True, False):
+        w = np.zeros((2, 1, nz))
+        w[:, :, :-1] = dz[:-1] / dt if up else -dz[1:] / dt
+        new = phi + dt * oracle.advect_tvd(c, np.zeros_like(w), np.zeros_like(w), w, phi, dt)
+        if up:
+            Mn = np.concatenate([np.zeros((2, 1, 1)), M[:, :, :-1]], axis=2)
+            Mn[:, :, -1] += M[:, :, -1]
+        else:
+            Mn = np.concatenate([M[:, :, 1:], np.zeros((2, 1, 1))], axis=2)
+            Mn[:, :, 0] += M[:, :, 0]
+        np.testing.assert_allclose(new * dz, Mn, rtol=0, atol=1e-13)
+
+
+def quad_cell_means(x0, h, a, b, q):
+    """Cell means over [x0 - h/2, x0 + h/2] of a + b x + q x^2."""
+    P = lambda x: a * x + b * x * x / 2 + q * x ** 3 / 3
+    return (P(x0 + h / 2) - P(x0 - h / 2)) / h
+
+
+def pin_tvd_quadratic_exact():
+    # QUICKEST is exact on the cell means of a parabola; on a monotone one the
+    # limiter leaves it alone, so one step equals the translated cell means
+    a, b, q = 3.0, 0.7, 0.02
+    for axis, n in ((0, 48), (1, 40), (2, 36)):
+        shape = [2, 2, 2]
+        shape[axis] = n
+        if axis < 2:
+            c = oracle.Coeffs(2, 1.0, 1.0)
+        else:
+            c = tvd_column_coeffs(np.ones(n))
+        x = np.arange(n, dtype=float)
+        line = quad_cell_means(x, 1.0, a, b, q)
+        phi = np.broadcast_to(line.reshape([n if d == axis else 1 for d in range(3)]), shape).copy()
+        for cr in (0.25, 0.6, 0.9):
+            for U in (2.0, -2.0):
+                wind = [np.zeros(shape) for _ in range(3)]
+                wind[axis][:] = U
+                if axis == 2:
+                    wind[2][:, :, -1] = 0.0
+                dt = cr / abs(U)
+                new = phi + dt * oracle.advect_tvd(c, *wind, phi, dt)
+                exact = quad_cell_means(x - U * dt, 1.0, a, b, q)
+                got = np.moveaxis(new, axis, 0)[:, 0, 0]
+                lo, hi = 3, n - 3   # away from the periodic seam and the ground / lid
+                np.testing.assert_allclose(got[lo:hi], exact[lo:hi], rtol=1e-13, err_msg=f"axis {axis} c {cr} U {U}")
+
+
+def total_variation(line):
+    return float(np.abs(np.diff(np.r_[line, line[:1]])).sum())
+
+
+def pin_tvd_total_variation():
+    # one dimension, uniform flow, c <= 1: no new extrema and no growth of the
+    # total variation, on random and on step data
+    rng = np.random.default_rng(33)
+    for axis in (0, 1):
+        n = 40
+        shape = [1, 1, 1]
+        shape[axis] = n
+        c = oracle.Coeffs(1, 1.0, 1.0)
+        for trial in range(12):
+            line = rng.random(n) if trial % 2 else (np.arange(n) % 9 < 4) + 0.05 * rng.random(n)
+            for cr in (0.15, 0.5, 0.85, 1.0):
+                for U in (1.0, -1.0):
+                    wind = [np.zeros(shape) for _ in range(3)]
+                    wind[axis][:] = U
+                    p = line.reshape(shape).copy()
+                    for _ in range(4):
+                        new = p + cr * oracle.advect_tvd(c, *wind, p, cr)
+                        assert total_variation(new.ravel()) <= total_variation(p.ravel()) * (1 + 1e-14) + 1e-14
+                        assert new.max() <= line.max() + 1e-14 and new.min() >= line.min() - 1e-14
+                        p = new
+
+
+def pin_tvd_conservation_and_mirror():
+    rng = np.random.default_rng(34)
+    nx, ny, nz = 7, 6, 10
+    c = stretched(nz)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    u = u - 5 + 3 * rng.standard_normal(u.shape)
+    phi = rng.random((nx, ny, nz)) * 4
+    s, cond = oracle.advect_tvd(c, u, v, w, phi, dt=2.0, want_cond=True)
+    # flux form: the density-weighted sum of the sources is 0 (periodic sides,
+    # no flux through the ground or the lid)
+    W = (c.rho_n * c.dz)[None, None, :]
+    assert abs(np.sum(W * s)) <= 1e-13 * np.sum(W * cond)
+    # reflecting x (cell i -> nx-1-i; the face of u(i) -> that of u(nx-2-i),
+    # whose velocity changes sign) reflects the source
+    r = lambda f: f[::-1]
+    ur = -np.roll(u[::-1], -1, axis=0)
+    sr = oracle.advect_tvd(c, ur, r(v), r(w), r(phi), dt=2.0)
+    np.testing.assert_allclose(sr, r(s), rtol=0, atol=1e-13 * np.abs(s).max())
+    # the same reflection in y
+    sy = oracle.advect_tvd(c, u[:, ::-1], -np.roll(v[:, ::-1], -1, axis=1), w[:, ::-1], phi[:, ::-1], dt=2.0)
+    np.testing.assert_allclose(sy, s[:, ::-1], rtol=0, atol=1e-13 * np.abs(s).max())
+
+
+def pin_tvd_lid_and_points():
+    rng = np.random.default_rng(35)
+    nx, ny, nz = 5, 4, 7
+    c = stretched(nz)
+    u, v, w = rand_fields(rng, nx, ny, nz)
+    phi = rng.standard_normal((nx, ny, nz))
+    s, cond = oracle.advect_tvd(c, u, v, w, phi, dt=1.5, want_cond=True)
+    w2 = w.copy()
+    w2[:, :, -1] = 1e3                      # the lid value is never read
+    np.testing.assert_array_equal(oracle.advect_tvd(c, u, v, w2, phi, dt=1.5), s)
+    assert np.all(cond >= np.abs(s) * (1 - 1e-15))
+    pts = np.array([[i, j, k] for i in range(nx) for j in range(ny) for k in range(nz)][::3])
+    o, oc = oracle.tvd_points(c, u, v, w, phi, 1.5, pts)
+    np.testing.assert_array_equal(o, s[pts[:, 0], pts[:, 1], pts[:, 2]])
+    np.testing.assert_array_equal(oc, cond[pts[:, 0], pts[:, 1], pts[:, 2]])
+
+
 PINS = [pin_worked_examples, pin_lid_ignored, pin_coefficients, pin_uniform_flow, pin_energy, pin_skew_adjoint,
         pin_momentum_divergence_free, pin_momentum_identity, pin_continuum_second_order,
         pin_adjoint_dot, pin_adjoint_bruteforce, pin_cond_and_points,
         pin_euler_energy_step, pin_euler_closed_forms, pin_euler_fixed_point_and_steps, pin_adjoint_cond,
         pin_scalar_worked_examples, pin_scalar_uniform_and_centred, pin_scalar_energy_and_skew,
-        pin_scalar_divergence_identity, pin_scalar_continuum_second_order, pin_scalar_lid_and_points]
+        pin_scalar_divergence_identity, pin_scalar_continuum_second_order, pin_scalar_lid_and_points,
+        pin_tvd_worked_examples, pin_tvd_coefficients_and_constants, pin_tvd_courant_one_shift,
+        pin_tvd_quadratic_exact, pin_tvd_total_variation, pin_tvd_conservation_and_mirror, pin_tvd_lid_and_points]
 
 
 @pytest.mark.parametrize("pin", PINS + [pin_loop_gradient], ids=lambda f: f.__name__)
@@ -682,6 +866,28 @@ MUTANTS = {
                                  "                        gs[T->a][Q1] += fabs(sc * phi);"),
     "adjoint_cond_drops_phi": ("                        gs[T->a][Q1] += fabs(sc * phi);",
                                "                        gs[T->a][Q1] += fabs(sc);"),
+    "tvd_quick_coefficient": ("- (1.0 - c * c) / 6.0 * (pd - 2.0 * pc + pu);",
+                              "- 1.0 / 8.0 * (pd - 2.0 * pc + pu);"),
+    "tvd_courant_half": ("    return 0.5 * (pc + pd) - 0.5 * c * (pd - pc)",
+                         "    return 0.5 * (pc + pd) - 0.25 * c * (pd - pc)"),
+    "tvd_extrema_unlimited": ("    if (!monotone) return pc;",
+                              "    if (!monotone) return quickest(pu, pc, pd, c);"),
+    "tvd_no_courant_bound": ("    double top = (c > tc) ? tc / c : 1.0;   /* min(1, tc / c) */",
+                             "    double top = 1.0;"),
+    "tvd_no_lower_bound": ("    if (tf < tc) tf = tc;",
+                           "    (void)0;"),
+    "tvd_negative_far_cell": ("    return ultimate(pr2, pr, pl, c);",
+                              "    return ultimate(pl2, pr, pl, c);"),
+    "tvd_courant_downwind_width": ("        c = fabs(a) * g->dt / g->dz[a >= 0.0 ? k - 1 : k];",
+                                   "        c = fabs(a) * g->dt / g->dz[k];"),
+    "tvd_fz1_density": ("        fz1[k] = (k > 0) ? rhow[k - 1] / (rhon[k] * dz[k]) : 0.0;",
+                        "        fz1[k] = (k > 0) ? rhon[k - 1] / (rhon[k] * dz[k]) : 0.0;"),
+    "tvd_ground_far_cell": ("                     k + 1 < nz ? tat(g, p, i, j, k + 1) : 0.0, k >= 2, k + 1 < nz, &m);",
+                            "                     k + 1 < nz ? tat(g, p, i, j, k + 1) : 0.0, 1, k + 1 < nz, &m);"),
+    "tvd_y_inflow_sign": ("    s = s + a * f / g->dy;",
+                          "    s = s - a * f / g->dy;"),
+    "tvd_x_face_shift": ("    f = tvd_face(a, c, tat(g, p, i - 1, j, k), tat(g, p, i, j, k), tat(g, p, i + 1, j, k),\n                 tat(g, p, i + 2, j, k), 1, 1, &m);",
+                         "    f = tvd_face(a, c, tat(g, p, i - 2, j, k), tat(g, p, i - 1, j, k), tat(g, p, i, j, k),\n                 tat(g, p, i + 1, j, k), 1, 1, &m);"),
 }
 
 
