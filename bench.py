@@ -304,6 +304,7 @@ def run_gpu(args):
 
     for name, fn in (("small_latency", lambda: bench_small_latency(args, world)),
                      ("scalars", lambda: bench_scalars(args, world, hbm)),
+                     ("tvd", lambda: bench_tvd(args, world, hbm)),
                      ("paper_strong_f32", lambda: bench_paper_strong(args, world, hbm)),
                      ("fused_step", lambda: bench_fused_step(args, world, hbm)),
                      ("batched", lambda: bench_batched(args, world, hbm)),
@@ -464,6 +465,47 @@ def bench_scalars(args, world, hbm):
         out[key] = {"value": world * pts * n * steps / tot, "unit": "scalar values/s",
                     "kernel_ms": round(kms, 4), "bytes_per_point": bpp,
                     "hbm_frac": round(bpp * pts / (kms * 1e-3) / 1e9 / hbm, 4)}
+        del m, U, P, S
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_tvd(args, world, hbm):
+    """The positivity-preserving ULTIMATE-QUICKEST scheme on theta + 5 q over
+    1024 x 1024 x 128 (dt 2 s: Courant numbers around 0.4 at dx 25 m), one
+    launch per step; FP64 (native), FP32 and BF16 storage.  Rate = scalar values
+    produced per second; compulsory bytes count the wind once per launch."""
+    import torch
+    from paper_2009_12850_b300 import api
+    wl, n, dt = WL, 6, 2.0
+    wind = synthetic.fields_for(wl)
+    phis = synthetic.scalar_fields(wl.nx, wl.ny, wl.nz, n, wl.seed + 100)
+    pts = wl.points
+    out = {"workload": f"{wl.name}, theta + 5 q, dt {dt} s", "scalars": n}
+    for dtype in ("f64", "f32", "bf16"):
+        m = api.Mesh(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, dtype=dtype)
+        U = [m.from_interior(a) for a in wind]
+        P = [m.from_interior(a) for a in phis]
+        S = [m.empty_out() for _ in range(n)]
+        stream = torch.cuda.current_stream()
+
+        def step(rec):
+            if rec is None:
+                m.advect_tvd(*U, P, dt, S, stream=stream)
+                return
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.advect_tvd(*U, P, dt, S, stream=stream)
+            b.record(stream)
+            rec.append((a, b))
+        steps = max(3, args.steps // 2)
+        tot, kms = time_steps(step, steps, 3, world)
+        assert m.device_status() == 0
+        ei, eo = SCALAR_BYTES[dtype]
+        bpp = 3 * ei + n * (ei + eo)
+        out[dtype] = {"value": world * pts * n * steps / tot, "unit": "scalar values/s",
+                      "kernel_ms": round(kms, 4), "bytes_per_point": bpp,
+                      "hbm_frac": round(bpp * pts / (kms * 1e-3) / 1e9 / hbm, 4)}
         del m, U, P, S
         torch.cuda.empty_cache()
     return out

@@ -260,6 +260,33 @@ pw_status pw_advect_scalars(const pw_mesh *mesh, const void *u, const void *v, c
 pw_status pw_advect_scalars_step(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
                                  const void *const *phi, void *const *phin, double dt, void *stream);
 
+/* The positivity-preserving scheme named beside PW (section 3.1, ULTIMATE;
+ * section 4 sizes it at about sixteen times the PW work), for n cell-centred
+ * scalars, in flux form on the C-grid:
+ *  s = (u(i-1) f_x(i-1) - u(i) f_x(i)) / dx + (v(j-1) f_y(j-1) - v(j) f_y(j)) / dy
+ *    + fz1(k) w(k-1) f_z(k-1) - fz2(k) w(k) f_z(k),
+ *  fz1(k) = rho_w(k-1)/(rho_n(k) dz(k)), fz2(k) = rho_w(k)/(rho_n(k) dz(k)),
+ * f_x(i) being the face value of phi on the face between cells i and i+1 where
+ * u(i) sits (f_y, f_z alike); the ground face w(-1) and the lid w(nz-1) carry
+ * no flux.  Face value (Leonard's ULTIMATE-QUICKEST): for velocity a, the
+ * upwind cell C, the downwind cell D and the far-upwind cell U (one beyond C),
+ * c = |a| dt / (width of C: dx, dy or dz(C)),
+ *  q = (phi_C + phi_D)/2 - c (phi_D - phi_C)/2 - (1 - c^2)/6 (phi_D - 2 phi_C + phi_U),
+ * held, where phi_C lies strictly between phi_U and phi_D, between phi_C and
+ * min(phi_D, phi_U + (phi_C - phi_U)/c) in the direction of phi_D (the bound
+ * toward phi_D applied first, so for c > 1 the face takes phi_C); elsewhere,
+ * and where U would lie below the ground or above the lid, f = phi_C.
+ * dt (> 0, finite) is the step the Courant numbers are taken for.  Halos of
+ * u, v, w and of every phi[a] must be filled (the scheme reads two cells
+ * along x and y).  phi and sphi are HOST arrays of n device pointers
+ * (1 <= n <= PW_MAX_SCALARS) in the mesh layout; sphi[a] has the source type
+ * of the mesh dtype (binary64 for PW_F64, bfloat16 for PW_BF16_OUT, binary32
+ * otherwise); beta as in pw_advect.  Arithmetic: native FP64 for PW_F64 (both
+ * algorithms), FP32 otherwise.  No output may alias an input or another
+ * output.  Returns PW_ERR_ARG for bad arguments; timeouts as pw_advect. */
+pw_status pw_advect_tvd(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
+                        const void *const *phi, void *const *sphi, double dt, int beta, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Fields in host memory: the step with its copies overlapped (the hybrid
  * offload of sections 3 and 3.1, where u, v, w go to the device every timestep

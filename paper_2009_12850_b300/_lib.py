@@ -65,6 +65,7 @@ _SIGS = {
     "pw_advect_step": ([_vp] + [_vp] * 6 + [_d, _vp], _i),
     "pw_advect_scalars_step": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _vp], _i),
     "pw_advect_scalars": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp], _i),
+    "pw_advect_tvd": ([_vp] * 4 + [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i, _vp], _i),
     "pw_pipeline_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
     "pw_pipeline_destroy": ([_vp], None),
     "pw_pipeline_slab": ([_vp, _ip, _ip], _i),
@@ -194,6 +195,12 @@ def pw_advect_scalars(mesh, u, v, w, phi, sphi, beta, stream):
     """phi, sphi: sequences of device pointers (one per scalar)."""
     check(_c.pw_advect_scalars(mesh, u, v, w, len(phi), _ptrs(phi), _ptrs(sphi), int(beta), stream),
           "pw_advect_scalars")
+
+
+def pw_advect_tvd(mesh, u, v, w, phi, sphi, dt, beta, stream):
+    """phi, sphi: sequences of device pointers (one per scalar)."""
+    check(_c.pw_advect_tvd(mesh, u, v, w, len(phi), _ptrs(phi), _ptrs(sphi), float(dt), int(beta), stream),
+          "pw_advect_tvd")
 
 
 SLAB_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)

@@ -149,6 +149,19 @@ class Mesh:
                             [self._check(s, "sphi", True) for s in sources], beta, _stream(stream))
         return sources
 
+    def advect_tvd(self, u, v, w, phis, dt, sources=None, beta=0, stream=None):
+        """ULTIMATE-QUICKEST (flux-form, positivity-preserving) sources of the
+        cell-centred scalars phis (halos filled) advected by (u, v, w) over a
+        step dt; returns the list of sources."""
+        phis = list(phis)
+        sources = [self.empty_out() for _ in phis] if sources is None else list(sources)
+        if len(sources) != len(phis):
+            raise ValueError("one source tensor per scalar")
+        L.pw_advect_tvd(self.handle, self._check(u, "u"), self._check(v, "v"), self._check(w, "w"),
+                        [self._check(p, "phi") for p in phis],
+                        [self._check(s, "sphi", True) for s in sources], dt, beta, _stream(stream))
+        return sources
+
     def step_scalars(self, u, v, w, phis, outs=None, dt=1.0, stream=None):
         """Fused forward Euler step of the scalars: outs[a] = phis[a] + dt s(phis[a]),
         halos included; returns outs."""

@@ -102,6 +102,22 @@ def test_advect_and_scalars_write_only_their_outputs(pw, shape, dtype, algo):
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "bf16_out"])
+def test_tvd_writes_only_its_outputs(pw, shape, dtype):
+    m = pw.Mesh(*shape, 45.0, 35.0, dtype=dtype)
+    U = fields(pw, m, 511)
+    P = fields(pw, m, 512, n=3, scalars=True)
+    su, sp = snapshot(U), snapshot(P)
+    SP = sources(m, 3)
+    for beta in (0, 1):
+        m.advect_tvd(*(g.t for g in U), [g.t for g in P], 4.0, [g.t for g in SP], beta=beta)
+        torch.cuda.synchronize()
+        assert m.device_status() == 0
+        assert unchanged(U, su) and unchanged(P, sp)
+        assert written_only_inside(m, SP)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("dtype,algo", KINDS)
 def test_fused_steps_stay_in_their_fields(pw, shape, dtype, algo):
     m = pw.Mesh(*shape, 45.0, 35.0, dtype=dtype, algo=algo)
