@@ -23,12 +23,14 @@
 // in x, y and z; the mesh's halos are two wide).  A CTA owns TJ rows x 32
 // levels, one level per thread.  Each step takes the newest plane p (column
 // i0-2+p) and
-//   1. evaluates the y and z face fluxes of that plane, (TJ+1) x 32 and
-//      TJ x 33 faces shared out over the CTA, into shared memory;
-//   2. after a barrier, forms each point's y + z flux divergence D (held two
+//   1. evaluates the y and z face fluxes of that plane: each thread the faces
+//      south of and below its point, warps 0 and 1 also the faces north of the
+//      last row and above the top level, into one of two shared-memory sets;
+//   2. after the step's one CTA barrier (which also frees plane p's ring slot
+//      for plane p + NS), forms each point's y + z flux divergence D (held two
 //      steps in registers);
 //   3. evaluates the x face flux between columns p-3 and p-2 from the thread's
-//      own register window phi(p-3 .. p) and writes column p-2's source.
+//      own register window phi(p-3 .. p) and writes column p-2's source;
 // so each point costs one x face and about 2.2 y/z faces instead of six.
 #include <algorithm>
 #include <type_traits>
@@ -40,11 +42,8 @@
 
 struct PwTvdGeom {
     int nx, ny, nz, nzp;
-    int kb;            // TMA box k extent: 32 + 2 h
-    int h;             // k halo in elements (16 bytes)
     int ti;            // columns marched per CTA
     int nkc;           // k chunks
-    int fs;            // elements between the u, v, w, phi planes of a slot (128-byte aligned)
     long long si, sj;  // strides of the sources (elements)
     double dtdx, dtdy; // dt/dx, dt/dy
     double rdx, rdy;   // 1/dx, 1/dy
@@ -56,55 +55,77 @@ struct PwTvdSet {
     void *out[PW_MAX_SCALARS];
 };
 
-// a * f for the face between cells L and R (phi at L-1, L, R, R+1), velocity a,
-// cf = dt / width of the upwind cell; far_ok: the far upwind cell exists
+// compile-time slot geometry of a storage type: k halo H (16 bytes), box k
+// extent KB, elements between the u, v, w, phi planes of a slot (128-byte aligned)
+template <typename TS, int TJ>
+struct PwTvdShape {
+    static constexpr int H = 16 / (int)sizeof(TS);
+    static constexpr int KB = PW_TVD_KC + 2 * H;
+    static constexpr int PER128 = 128 / (int)sizeof(TS);
+    static constexpr int FS = ((TJ + 4) * KB + PER128 - 1) / PER128 * PER128;
+};
+
 template <typename TC>
-__device__ __forceinline__ TC pw_tvd_flux(TC a, TC cf, TC pl2, TC pl, TC pr, TC pr2, bool far_ok) {
+__device__ __forceinline__ TC pw_tvd_div(TC x, TC y) {
+    if constexpr (std::is_same<TC, float>::value) return __fdividef(x, y);
+    else return x / y;
+}
+
+// a * f for the face between cells L and R (phi at L-1, L, R, R+1), velocity a;
+// cfp, cfn: dt / width of the upwind cell for a >= 0 (cell L) and a < 0 (cell R);
+// farp, farn: the far upwind cell exists for a >= 0 (L-1) and a < 0 (R+1).
+// Branch-free: both clamps are formed and the flow decides by selection (the
+// quotient is only selected where c |phi_D - phi_U| > |phi_C - phi_U|, so c > 0).
+template <typename TC>
+__device__ __forceinline__ TC pw_tvd_flux(TC a, TC cfp, TC cfn, TC pl2, TC pl, TC pr, TC pr2, bool farp,
+                                          bool farn) {
     const bool pos = a >= TC(0);
     const TC pu = pos ? pl2 : pr2, pc = pos ? pl : pr, pd = pos ? pr : pl;
-    TC f = pc;
+    const TC c = fabs(a) * (pos ? cfp : cfn);
     const bool up = pu < pc && pc < pd, dn = pd < pc && pc < pu;
-    if (far_ok && (up || dn)) {
-        const TC c = (pos ? a : -a) * cf;
-        const TC q = TC(0.5) * (pc + pd) - TC(0.5) * c * (pd - pc) -
-                     (TC(1) - c * c) * (TC(1) / TC(6)) * ((pd - pc) - (pc - pu));
-        const TC del = pd - pu, dc = pc - pu;
-        // upper end: phi_D, or phi_U + (phi_C - phi_U)/c where that is nearer
-        TC hi = pd;
-        if (c * (up ? del : -del) > (up ? dc : -dc)) hi = pu + dc / c;
-        f = up ? fmax(fmin(q, hi), pc) : fmin(fmax(q, hi), pc);
-    }
+    const bool mono = (pos ? farp : farn) && (up || dn);
+    const TC q = TC(0.5) * (pc + pd) - TC(0.5) * c * (pd - pc) -
+                 (TC(1) - c * c) * (TC(1) / TC(6)) * ((pd - pc) - (pc - pu));
+    const TC del = pd - pu, dc = pc - pu;
+    // upper end: phi_D, or phi_U + (phi_C - phi_U)/c where that is nearer
+    const TC hi = c * fabs(del) > fabs(dc) ? pu + pw_tvd_div(dc, c) : pd;
+    const TC f = mono ? (up ? fmax(fmin(q, hi), pc) : fmin(fmax(q, hi), pc)) : pc;
     return a * f;
 }
 
-// TJ rows per CTA, TS storage, TC arithmetic, TO source type
+// TJ rows per CTA, TS storage, TC arithmetic, TO source type.
+//
+// Face schedule of a step, per thread (tr, tl) = (row, level in the chunk):
+//   A: the y face south of its point (rows j-1 | j),
+//   B: the z face below its point (levels k-1 | k),
+//   C: warp 0 takes the y faces north of the last row, lanes 0..TJ-1 of warp 1
+//      the z faces above the chunk's top level;
+// a thread keeps its own A and B fluxes and reads the north and upper ones
+// from shared memory after the step's barrier.
 template <typename TS, typename TC, typename TO, int TJ>
 __global__ void __launch_bounds__(TJ * PW_TVD_KC)
 pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
              const __grid_constant__ CUtensorMap mw, const __grid_constant__ PwTvdSet set,
              const double *__restrict__ coef64, const PwTvdGeom g, int beta, int *__restrict__ status) {
     constexpr int KC = PW_TVD_KC, NS = PW_TVD_NS, ROWS = TJ + 4;
+    using SH = PwTvdShape<TS, TJ>;
+    constexpr int H = SH::H, KB = SH::KB, FS = SH::FS;
     constexpr int NGY = (TJ + 1) * KC, NGZ = TJ * (KC + 1);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if (pw_cta_failed(status)) return;
     const int sc = blockIdx.x / g.nkc, kchunk = blockIdx.x % g.nkc;
     const int j0 = blockIdx.y * TJ, i0 = blockIdx.z * g.ti, k0 = kchunk * KC;
-    const int fs = g.fs;
     TS *planes = reinterpret_cast<TS *>(smem_raw);
-    TC *Gy = reinterpret_cast<TC *>(smem_raw + (size_t)NS * 4 * fs * sizeof(TS));
-    TC *Gz = Gy + NGY;
-    TC *cft = Gz + NGZ;  // dt / dz(K) for K = k0-1 .. k0+KC (0 outside the column)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(cft) +
-                                                  ((KC + 2) * sizeof(TC) + 15) / 16 * 16);
+    TC *Gbuf = reinterpret_cast<TC *>(smem_raw + (size_t)NS * 4 * FS * sizeof(TS));  // two sets of faces
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Gbuf + 2 * (NGY + NGZ));
 
-    const int tid = threadIdx.x, nt = TJ * KC;
+    const int tid = threadIdx.x;
     const int tr = tid / KC, tl = tid % KC;
     const int j = j0 + tr, k = k0 + tl;
     const bool active = j < g.ny && k < g.nz;
     const int i_end = min(i0 + g.ti, g.nx);
     const int nplanes = i_end - i0 + 4;
-    const uint32_t plane_bytes = (uint32_t)(ROWS * g.kb * sizeof(TS));
-    const uint32_t slot_bytes = 4u * plane_bytes;
+    constexpr uint32_t slot_bytes = 4u * ROWS * KB * sizeof(TS);
 
     if (tid == 0) {
         pw_prefetch_map(&mu);
@@ -114,22 +135,18 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
         for (int s = 0; s < NS; s++) pw_mbar_init(&bars[s], 1);
         pw_fence_barrier_init();
     }
-    for (int t = tid; t < KC + 2; t += nt) {
-        const int K = k0 - 1 + t;
-        cft[t] = (K >= 0 && K < g.nz) ? (TC)(g.dt / coef64[K]) : TC(0);
-    }
     __syncthreads();
 
-    auto slot = [&](int p) { return planes + (size_t)(p % NS) * 4 * fs; };
+    auto slot = [&](int p) { return planes + (size_t)(p % NS) * 4 * FS; };
     auto issue = [&](int p) {
         const int s = p % NS;
         TS *dst = slot(p);
         pw_mbar_expect_tx(&bars[s], slot_bytes);
-        const int c0 = k0 - g.h, c1 = j0, c2 = i0 + p;  // (k0-h, j0-2, i0-2+p) + the halo offset 2
+        const int c0 = k0 - H, c1 = j0, c2 = i0 + p;  // (k0-H, j0-2, i0-2+p) + the halo offset 2
         pw_tma_load_3d(dst, &mu, c0, c1, c2, &bars[s]);
-        pw_tma_load_3d(dst + fs, &mv, c0, c1, c2, &bars[s]);
-        pw_tma_load_3d(dst + 2 * fs, &mw, c0, c1, c2, &bars[s]);
-        pw_tma_load_3d(dst + 3 * fs, &set.phi[sc], c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + FS, &mv, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + 2 * FS, &mw, c0, c1, c2, &bars[s]);
+        pw_tma_load_3d(dst + 3 * FS, &set.phi[sc], c0, c1, c2, &bars[s]);
     };
     int issued = 0;
     if (tid == 0) {
@@ -143,12 +160,28 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
             atomicExch(status, (int)PW_ERR_TIMEOUT);
         }
     };
+    auto dtdz = [&](int K) { return (K >= 0 && K < g.nz) ? (TC)(g.dt / coef64[K]) : TC(0); };
 
     const TC cfx = (TC)g.dtdx, cfy = (TC)g.dtdy, rdx = (TC)g.rdx, rdy = (TC)g.rdy;
     const TC fz1 = (k > 0 && k < g.nz) ? (TC)(4.0 * coef64[6 * g.nz + k]) : TC(0);
     const TC fz2 = (k < g.nz - 1) ? (TC)(4.0 * coef64[7 * g.nz + k]) : TC(0);
-    const int h = g.h, L = g.kb;
-    const int own = (tr + 2) * L + h + tl;  // this thread's (j, k) in a plane
+    // B: the face below level k (K = k-1): exists for 1 <= k <= nz-1
+    const bool zB = k >= 1 && k < g.nz;
+    const TC cfBp = dtdz(k - 1), cfBn = dtdz(k);
+    const bool farBp = k >= 2, farBn = k + 1 < g.nz;
+    // C: warp 0: the y face north of row TJ-1; warp 1, lane r < TJ: the z face
+    // above level k0+KC-1 of row r
+    const int roleC = tid < KC ? 1 : (tid < KC + TJ ? 2 : 0);
+    const int rC = tid - KC;  // row of a role-2 thread
+    const int KT = k0 + KC - 1;
+    const bool zC = KT < g.nz - 1;
+    const TC cfCp = dtdz(KT), cfCn = dtdz(KT + 1);
+    const bool farCn = KT + 2 < g.nz;
+
+    const int oA = tr * KB + H + tl;             // A: phi rows j-2 .. j+1, v(j-1) one row down
+    const int oB = (tr + 2) * KB + H + tl - 2;   // B: levels k-2 .. k+1 of row j; w(k-1)
+    const int own = (tr + 2) * KB + H + tl;      // this thread's (j, k)
+    const int oC = roleC == 1 ? TJ * KB + H + tl : (rC + 2) * KB + H + KC - 2;
 
     TO *out = reinterpret_cast<TO *>(set.out[sc]);
     TC ph[4] = {TC(0), TC(0), TC(0), TC(0)};  // phi at columns c-1 .. c+2 (own point)
@@ -157,60 +190,57 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
     TC Gx_w = TC(0);                          // x flux on the west face of the column written next
 
     for (int p = 0; p < nplanes; p++) {
+        // every thread waits for plane p itself; the step's one CTA barrier
+        // (after the face fluxes) shares the outcome
         const bool ok = pw_mbar_wait_bounded(&bars[p % NS], (uint32_t)((p / NS) & 1));
-        if (!__syncthreads_and(ok)) {
-            give_up(p);
-            return;
-        }
-        // every thread is done with plane p-1 and with the face arrays
-        if (tid == 0 && p >= 1 && p - 1 + NS < nplanes) {
-            issue(p - 1 + NS);
-            issued = p + NS;
-        }
+        TC *Gy = Gbuf + (p & 1) * (NGY + NGZ), *Gz = Gy + NGY;
         const TS *P = slot(p);
-        const TS *Pu = P, *Pv = P + fs, *Pw = P + 2 * fs, *Pp = P + 3 * fs;
+        const TS *Pu = P, *Pv = P + FS, *Pw = P + 2 * FS, *Pp = P + 3 * FS;
         const bool faces = p >= 2 && p < nplanes - 2;  // columns i0 .. i_end-1
+        const TC pC = pw_to<TC>(Pp[own]);
+        TC GA = TC(0), GB = TC(0);
         if (faces) {
-            for (int e = tid; e < NGY + NGZ; e += nt) {
-                if (e < NGY) {
-                    // face between rows j0+r-1 and j0+r, level k0+l (slot rows r .. r+3)
-                    const int r = e / KC, l = e % KC;
-                    const TS *b = Pp + r * L + h + l;
-                    Gy[e] = pw_tvd_flux<TC>(pw_to<TC>(Pv[(r + 1) * L + h + l]), cfy, pw_to<TC>(b[0]),
-                                            pw_to<TC>(b[L]), pw_to<TC>(b[2 * L]), pw_to<TC>(b[3 * L]), true);
-                } else {
-                    // face between levels K = k0+l-1 and K+1, row j0+r
-                    const int q = e - NGY, r = q / (KC + 1), l = q % (KC + 1);
-                    const int K = k0 + l - 1;
-                    TC G = TC(0);
-                    if (K >= 0 && K < g.nz - 1) {
-                        const TS *b = Pp + (r + 2) * L + h + l - 2;  // levels K-1 .. K+2
-                        const TC a = pw_to<TC>(Pw[(r + 2) * L + h + l - 1]);
-                        const bool pos = a >= TC(0);
-                        const bool far = pos ? K >= 1 : K + 2 < g.nz;
-                        G = pw_tvd_flux<TC>(a, pos ? cft[l] : cft[l + 1], pw_to<TC>(b[0]), pw_to<TC>(b[1]),
-                                            pw_to<TC>(b[2]), pw_to<TC>(b[3]), far);
-                    }
-                    Gz[q] = G;
-                }
+            GA = pw_tvd_flux<TC>(pw_to<TC>(Pv[oA + KB]), cfy, cfy, pw_to<TC>(Pp[oA]), pw_to<TC>(Pp[oA + KB]), pC,
+                                 pw_to<TC>(Pp[oA + 3 * KB]), true, true);
+            if (zB)
+                GB = pw_tvd_flux<TC>(pw_to<TC>(Pw[oB + 1]), cfBp, cfBn, pw_to<TC>(Pp[oB]), pw_to<TC>(Pp[oB + 1]),
+                                     pC, pw_to<TC>(Pp[oB + 3]), farBp, farBn);
+            if (roleC == 1) {
+                Gy[TJ * KC + tl] = pw_tvd_flux<TC>(pw_to<TC>(Pv[oC + KB]), cfy, cfy, pw_to<TC>(Pp[oC]),
+                                                   pw_to<TC>(Pp[oC + KB]), pw_to<TC>(Pp[oC + 2 * KB]),
+                                                   pw_to<TC>(Pp[oC + 3 * KB]), true, true);
+            } else if (roleC == 2) {
+                Gz[rC * (KC + 1) + KC] =
+                    zC ? pw_tvd_flux<TC>(pw_to<TC>(Pw[oC + 1]), cfCp, cfCn, pw_to<TC>(Pp[oC]), pw_to<TC>(Pp[oC + 1]),
+                                         pw_to<TC>(Pp[oC + 2]), pw_to<TC>(Pp[oC + 3]), true, farCn)
+                       : TC(0);
             }
+            Gy[tr * KC + tl] = GA;
+            Gz[tr * (KC + 1) + tl] = GB;
         }
         // own values of the newest plane
         ph[0] = ph[1];
         ph[1] = ph[2];
         ph[2] = ph[3];
-        ph[3] = pw_to<TC>(Pp[own]);
+        ph[3] = pC;
         uw[0] = uw[1];
         uw[1] = uw[2];
         uw[2] = pw_to<TC>(Pu[own]);
-        __syncthreads();
+        if (!__syncthreads_and(ok)) {
+            give_up(p);
+            return;
+        }
+        // every thread is done reading plane p (faces and its own values): its
+        // slot takes plane p + NS
+        if (tid == 0 && p + NS < nplanes) {
+            issue(p + NS);
+            issued = p + NS + 1;
+        }
         TC D = TC(0);
-        if (faces)
-            D = (Gy[tr * KC + tl] - Gy[(tr + 1) * KC + tl]) * rdy + fz1 * Gz[tr * (KC + 1) + tl] -
-                fz2 * Gz[tr * (KC + 1) + tl + 1];
+        if (faces) D = (GA - Gy[(tr + 1) * KC + tl]) * rdy + fz1 * GB - fz2 * Gz[tr * (KC + 1) + tl + 1];
         if (p >= 3) {
             // x face between columns c = i0+p-4 and c+1: phi(c-1 .. c+2), u(c)
-            const TC Gx = pw_tvd_flux<TC>(uw[0], cfx, ph[0], ph[1], ph[2], ph[3], true);
+            const TC Gx = pw_tvd_flux<TC>(uw[0], cfx, cfx, ph[0], ph[1], ph[2], ph[3], true, true);
             if (p >= 4 && active) {
                 const int i = i0 + p - 4;
                 const TC s = (Gx_w - Gx) * rdx + D2;
@@ -244,17 +274,14 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
                                  cudaStream_t st, int tile_i) {
     constexpr int KC = PW_TVD_KC, NS = PW_TVD_NS;
     PwTvdGeom g;
+    using SH = PwTvdShape<TS, TJ>;
     g.nx = m->nx;
     g.ny = m->ny;
     g.nz = m->nz;
     g.nzp = m->nzp;
-    g.h = 16 / (int)sizeof(TS);
-    g.kb = KC + 2 * g.h;
     g.nkc = (m->nz + KC - 1) / KC;
     const long tiles = (long)((m->ny + TJ - 1) / TJ) * g.nkc * n;
     g.ti = pw_fit_tile_i(m, tile_i, tiles);
-    const int per128 = 128 / (int)sizeof(TS);
-    g.fs = ((TJ + 4) * g.kb + per128 - 1) / per128 * per128;
     g.si = m->si;
     g.sj = m->sj;
     g.dtdx = dt / m->dx;
@@ -262,21 +289,20 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
     g.rdx = 1.0 / m->dx;
     g.rdy = 1.0 / m->dy;
     g.dt = dt;
-    const size_t smem = (size_t)NS * 4 * g.fs * sizeof(TS) +
-                        ((size_t)((TJ + 1) * KC + TJ * (KC + 1)) * sizeof(TC)) +
-                        ((KC + 2) * sizeof(TC) + 15) / 16 * 16 + NS * sizeof(uint64_t);
+    const size_t smem = (size_t)NS * 4 * SH::FS * sizeof(TS) +
+                        (size_t)2 * ((TJ + 1) * KC + TJ * (KC + 1)) * sizeof(TC) + NS * sizeof(uint64_t);
     if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "tvd: %zu bytes of shared memory", smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
     for (int q = 0; q < 3; q++) {
-        pw_status s = pw_make_field_map(&maps[q], f[q], m->dtype, m->nx, m->ny, m->nzp, pw_kdim(m->nz, q), g.kb,
+        pw_status s = pw_make_field_map(&maps[q], f[q], m->dtype, m->nx, m->ny, m->nzp, pw_kdim(m->nz, q), SH::KB,
                                         TJ + 4);
         if (s != PW_OK) return s;
     }
     PwTvdSet set;
     memset(&set, 0, sizeof(set));
     for (int q = 0; q < n; q++) {
-        pw_status s = pw_make_field_map(&set.phi[q], phi[q], m->dtype, m->nx, m->ny, m->nzp, m->nz, g.kb, TJ + 4);
+        pw_status s = pw_make_field_map(&set.phi[q], phi[q], m->dtype, m->nx, m->ny, m->nzp, m->nz, SH::KB, TJ + 4);
         if (s != PW_OK) return s;
         set.out[q] = sphi[q];
     }
