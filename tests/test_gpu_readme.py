@@ -34,3 +34,7 @@ def test_readme_quick_start_runs():
         compare(name, m.interior(got).double().cpu().numpy(), r, c, TOL_F64, TOL_F64)
     assert len(scope["s_phi"]) == 6
     assert all(np.isfinite(m.interior(t).double().cpu().numpy()).all() for t in scope["s_phi"])
+    # the ULTIMATE-QUICKEST sources of theta against the oracle
+    theta = synthetic.scalar_fields(nx, ny, nz, 6, seed=2)[0]
+    ref, cond = oracle.advect_tvd(oracle.Coeffs(nz, 25.0, 25.0), *f, theta, 2.0, want_cond=True)
+    compare("s_tvd", m.interior(scope["s_tvd"][0]).double().cpu().numpy(), ref, cond, TOL_F64, TOL_F64)
