@@ -230,8 +230,7 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     tile_j = tile_j < 256 / (g.kc / KV) ? tile_j : 256 / (g.kc / KV);
     if (tile_j < 1) tile_j = 1;
     g.tj = tile_j;
-    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
-    g.ti = tile_i;
+    const long tiles = (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc);
     g.ns = ns;
     g.plane_elems = (tile_j + 2) * g.kb;
     int per128 = 128 / (int)sizeof(TS);
@@ -252,6 +251,9 @@ static pw_status pw_launch_adjoint(const pw_mesh *m, const void *const *in, void
     }
     auto kern = pw_adjoint_march<TS, TC, KV>;
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // a CTA marches ti columns from ti + 2 planes
+    tile_i = pw_pick_tile_i(m, tile_i, tiles, pw_slots(m, kern, threads, smem), 2);
+    g.ti = tile_i;
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)((m->nz + g.kc - 1) / g.kc));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large");

@@ -291,7 +291,7 @@ pw_status pw_launch_adjoint_split(const pw_mesh *m, const void *const *in, void 
     g.kc = kc_one <= kc_max ? kc_one : kc_max;
     g.half = g.kc / 2;
     const int kb = g.kc + 4, cw = g.half + 2;
-    g.ti = pw_fit_tile_i(m, m->tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
+    const long tiles = (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc);
     g.rfs = ((tile_j + 2) * kb + 15) / 16 * 16;
     g.si = m->si;
     g.sj = m->sj;
@@ -311,6 +311,8 @@ pw_status pw_launch_adjoint_split(const pw_mesh *m, const void *const *in, void 
     auto kern = g.kc == kc_max ? (iso ? pw_adjoint_split_kernel<8, 32, true> : pw_adjoint_split_kernel<8, 32, false>)
                                : (iso ? pw_adjoint_split_kernel<8, 0, true> : pw_adjoint_split_kernel<8, 0, false>);
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // a CTA marches ti columns from ti + 2 planes
+    g.ti = pw_pick_tile_i(m, m->tile_i, tiles, pw_slots(m, kern, threads, smem), 2);
     dim3 grid((unsigned)((m->nz + g.kc - 1) / g.kc), (unsigned)((m->ny + tile_j - 1) / tile_j),
               (unsigned)((m->nx + g.ti - 1) / g.ti));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large");

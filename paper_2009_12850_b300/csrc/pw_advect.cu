@@ -63,8 +63,7 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
     // rows per CTA: as asked, but no more than 512 threads (long columns)
     tile_j = std::max(1, std::min(tile_j, 512 / (g.kc / KV)));
     g.tj = tile_j;
-    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
-    g.ti = tile_i;
+    const long tiles = (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc);
     g.ns = ns;
     g.plane_elems = (tile_j + 2) * g.kb;
     int per128 = 128 / (int)sizeof(TS);
@@ -91,6 +90,9 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
         else return pw_advect_march<TS, TC, TO, KV>;
     }();
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // a CTA marches ti columns from ti + 2 planes
+    tile_i = pw_pick_tile_i(m, tile_i, tiles, pw_slots(m, kern, threads, smem), 2);
+    g.ti = tile_i;
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)((m->nz + g.kc - 1) / g.kc));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");

@@ -350,8 +350,7 @@ static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v,
     g.half = g.kc / 2;
     g.kb = g.kc + 4;
     g.cw = g.half + 2;
-    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
-    g.ti = tile_i;
+    const long tiles = (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc);
     g.rfs = ((tile_j + 2) * g.kb + 15) / 16 * 16;  // 128-byte aligned TMA destinations
     g.cfs = (tile_j + 2) * g.cw;
     g.si = m->si;
@@ -385,6 +384,9 @@ static pw_status pw_launch_split(const pw_mesh *m, const void *u, const void *v,
     else kern = full ? PW_SPLIT_PICK(4, 64) : PW_SPLIT_PICK(4, 0);
 #undef PW_SPLIT_PICK
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // a CTA marches ti columns from ti + 2 planes
+    tile_i = pw_pick_tile_i(m, tile_i, tiles, pw_slots(m, kern, threads, smem), 2);
+    g.ti = tile_i;
     dim3 grid((unsigned)((m->nz + g.kc - 1) / g.kc), (unsigned)((m->ny + tile_j - 1) / tile_j),
               (unsigned)((m->nx + tile_i - 1) / tile_i));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_j or tile_i");

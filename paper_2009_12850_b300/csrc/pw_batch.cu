@@ -453,19 +453,27 @@ extern "C" pw_status pw_autotune(pw_mesh *m, const void *u, const void *v, const
     else cj = {2, 4, 8};
     float best = 1e30f;
     int bj = m->tile_j, bi = m->tile_i;
+    const int was_auto = m->tile_i_auto;
+    m->tile_i_auto = 0;  // time the candidates as given
     for (int a : cj)
         for (int c : ci) {
             float ms = 0;
             pw_status s = pw_time([&] { return pw_launch_advect(m, u, v, w, su, sv, sw, 0, st, a, c); }, st, &ms);
             if (s == PW_ERR_SHAPE) continue;  // candidate does not fit this mesh
-            if (s != PW_OK) return s;
+            if (s != PW_OK) {
+                m->tile_i_auto = was_auto;
+                return s;
+            }
             if (ms < best) {
                 best = ms;
                 bj = a;
                 bi = c;
             }
         }
-    if (best >= 1e30f) return pw_fail(PW_ERR_SHAPE, "no tile candidate fits this mesh");
+    if (best >= 1e30f) {
+        m->tile_i_auto = was_auto;
+        return pw_fail(PW_ERR_SHAPE, "no tile candidate fits this mesh");
+    }
     m->tile_j = bj;
     m->tile_i = bi;
     if (best_ms) *best_ms = best;

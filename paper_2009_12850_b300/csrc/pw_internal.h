@@ -27,6 +27,7 @@ struct pw_mesh {
     int *status;             // device: [0] timeout status (0 or PW_ERR_TIMEOUT), [1] lid flag,
                              // [2] split-range flag, [3] unused
     int tile_j, tile_i;      // stencil tile: rows per CTA, columns marched per CTA
+    int tile_i_auto;         // 1 while tile_i is the default (not set by the caller or the autotuner)
 };
 
 // words of the mesh status array
@@ -78,6 +79,43 @@ static inline int pw_fit_tile_i(const pw_mesh *m, int tile_i, long ctas_per_colu
     const long wave = 4L * m->num_sms;  // typical resident CTAs of the x-march kernels
     while (tile_i > 4 && ctas_per_column_tile * ((m->nx + tile_i - 1) / tile_i) < wave) tile_i = (tile_i + 1) / 2;
     return tile_i;
+}
+
+// Columns marched per CTA for an x-march launch of `tiles` CTAs per column
+// range, `slots` of which fit on the GPU at once (resident CTAs per SM x SMs),
+// each marching ti columns plus `prime` priming planes.  With the mesh's
+// default tile the count in [4, 2 tile_i] that minimises the launch time when
+// the CTAs run in waves: ceil(ctas / slots) waves, each as long as one CTA's
+// march (the longer count wins ties: fewer priming planes in all), so a grid
+// never ends in a nearly empty wave.  A tile set by the caller (or the
+// autotuner) keeps pw_fit_tile_i's rule.
+static inline int pw_pick_tile_i(const pw_mesh *m, int tile_i, long tiles, long slots, int prime) {
+    if (!m->tile_i_auto || slots < 1 || tiles < 1) return pw_fit_tile_i(m, tile_i, tiles);
+    const int hi = m->nx < 2 * tile_i ? m->nx : 2 * tile_i;
+    int lo = hi < 4 ? hi : 4;
+    while ((m->nx + lo - 1) / lo > 65535) lo++;  // grid dimension limit
+    int best = hi > lo ? hi : lo;
+    long long bestc = -1;
+    for (int ti = best; ti >= lo; ti--) {
+        const long long ctas = (long long)tiles * ((m->nx + ti - 1) / ti);
+        const long long c = ((ctas + slots - 1) / slots) * (ti + prime);
+        if (bestc < 0 || c < bestc) {
+            bestc = c;
+            best = ti;
+        }
+    }
+    return best;
+}
+
+// resident CTAs of a kernel on the whole GPU (0 if the query fails)
+template <typename K>
+static inline long pw_slots(const pw_mesh *m, K kern, int threads, size_t smem) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (long)occ * m->num_sms;
 }
 
 // launchers (pw_advect.cu / pw_adjoint.cu)

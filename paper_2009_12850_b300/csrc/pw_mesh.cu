@@ -2,6 +2,8 @@
 // fill, forward-Euler update with halo refresh, conservation reductions and
 // the error plumbing of the C-ABI.
 #include <math.h>
+
+#include <algorithm>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -249,6 +251,7 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
     // them): the double-float kernels run 8 rows x 32-level chunks per CTA
     m->tile_j = (m->dtype == PW_F64 && m->algo == PW_ALGO_F64_SPLIT) ? 8 : 4;
     m->tile_i = 64;
+    m->tile_i_auto = 1;
     double *tmp = nullptr;
     if ((e = cudaMalloc(&m->coef64, 12 * (size_t)nz * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&m->coef32, 4 * (size_t)nz * sizeof(float))) != cudaSuccess ||
@@ -369,6 +372,7 @@ extern "C" pw_status pw_mesh_set_tile(pw_mesh *m, int tile_j, int tile_i) {
         return pw_fail(PW_ERR_ARG, "tile_j must be in 1..32 and tile_i >= 1");
     m->tile_j = tile_j;
     m->tile_i = tile_i;
+    m->tile_i_auto = 0;
     return PW_OK;
 }
 
@@ -451,20 +455,37 @@ extern "C" pw_status pw_halo_periodic(const pw_mesh *m, void *f1, void *f2, void
 
 // ---------------------------------------------------------------------------
 // Adjoint of the periodic halo fill: every halo value is added onto the
-// interior value it copies and the halo is zeroed.  One thread per interior
-// element; it gathers from all its halo images, so there are no races.
+// interior value it copies and the halo is zeroed.  Only interior columns
+// within two of an x or y edge have halo images; one thread per element of
+// those columns gathers from all its images, so there are no races.  The
+// edge columns are enumerated directly: the nr edge rows (i < 2 or
+// i >= nx - 2; all rows when nx <= 4) with every j, then the other rows with
+// their nc edge columns (j < 2 or j >= ny - 2; all when ny <= 4).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int pw_edge_index(int q, int n) {  // q-th of the indices < 2 or >= n - 2
+    return n <= 4 ? q : (q < 2 ? q : n - 4 + q);
+}
+
 template <typename T>
 __global__ void pw_halo_fold_kernel(T *f0, T *f1, T *f2, int nx, int ny, int nz, int nzp) {
     T *f = blockIdx.y == 0 ? f0 : blockIdx.y == 1 ? f1 : f2;
-    int64_t n = (int64_t)nx * ny * nz;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int nr = nx < 4 ? nx : 4, nc = ny < 4 ? ny : 4;
+    const int64_t first = (int64_t)nr * ny;                 // columns of the edge rows
+    const int64_t ncols = first + (int64_t)(nx - nr) * nc;  // plus the edge columns of the others
+    const int64_t n = ncols * nz;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-        int k = (int)(e % nz);
-        int64_t col = e / nz;
-        int j = (int)(col % ny), i = (int)(col / ny);
-        bool ei = (i < 2) || (i >= nx - 2), ej = (j < 2) || (j >= ny - 2);
-        if (!ei && !ej) continue;
+        const int k = (int)(e % nz);
+        const int64_t q = e / nz;
+        int i, j;
+        if (q < first) {
+            i = pw_edge_index((int)(q / ny), nx);
+            j = (int)(q % ny);
+        } else {
+            const int64_t r = q - first;
+            i = 2 + (int)(r / nc);  // rows 2 .. nx-3 (nx > 4 here)
+            j = pw_edge_index((int)(r % nc), ny);
+        }
         T acc = T(0);
         for (int ih = i + 2 - ((i + 2) / nx) * nx; ih < nx + 4; ih += nx)
             for (int jh = j + 2 - ((j + 2) / ny) * ny; jh < ny + 4; jh += ny) {
@@ -490,7 +511,10 @@ extern "C" pw_status pw_halo_fold(const pw_mesh *m, void *f1, void *f2, void *f3
     }
     if (m->dtype != PW_F64 && m->dtype != PW_F32)
         return pw_fail(PW_ERR_DTYPE, "pw_halo_fold supports PW_F64 and PW_F32 meshes");
-    dim3 grid((unsigned)(m->num_sms * 4), (unsigned)n);
+    const long long nr = m->nx < 4 ? m->nx : 4, nc = m->ny < 4 ? m->ny : 4;
+    const long long elems = (nr * m->ny + (long long)(m->nx - nr) * nc) * m->nz;
+    const long long blocks = std::min<long long>((elems + 255) / 256, (long long)m->num_sms * 4);
+    dim3 grid((unsigned)std::max<long long>(blocks, 1), (unsigned)n);
     cudaStream_t st = (cudaStream_t)stream;
     void *a = f[0], *b = n > 1 ? f[1] : f[0], *c = n > 2 ? f[2] : f[0];
     if (m->dtype == PW_F64)

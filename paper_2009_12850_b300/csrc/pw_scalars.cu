@@ -232,8 +232,6 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     tile_j = tile_j < 512 / (g.kc / KV) ? tile_j : 512 / (g.kc / KV);
     if (tile_j < 1) tile_j = 1;
     g.tj = tile_j;
-    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * ((m->nz + g.kc - 1) / g.kc));
-    g.ti = tile_i;
     g.ns = NS;
     g.plane_elems = (tile_j + 2) * g.kb;
     const int per128 = 128 / (int)sizeof(TS);
@@ -280,6 +278,9 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     auto kern = pw_scalar_march<TS, TC, TO, KV, NS, PW_SCALAR_GMAX, STEP>;
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long ngroups = (n + group - 1) / group;
+    // as in the FP64 scalar kernel, the grid keeps the fill rule
+    tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * sg.nkc);
+    g.ti = tile_i;
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
               (unsigned)(sg.nkc * ngroups));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "grid too large; raise tile_i");

@@ -281,7 +281,6 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
     g.nzp = m->nzp;
     g.nkc = (m->nz + KC - 1) / KC;
     const long tiles = (long)((m->ny + TJ - 1) / TJ) * g.nkc * n;
-    g.ti = pw_fit_tile_i(m, tile_i, tiles);
     g.si = m->si;
     g.sj = m->sj;
     g.dtdx = dt / m->dx;
@@ -308,6 +307,8 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
     }
     auto kern = pw_tvd_march<TS, TC, TO, TJ>;
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // a CTA marches ti columns from ti + 4 planes
+    g.ti = pw_pick_tile_i(m, tile_i, tiles, pw_slots(m, kern, TJ * KC, smem), 4);
     // the scalar and the k chunk are the fastest grid indices: the CTAs of one
     // tile run together and share the wind and the k-halo levels through L2
     dim3 grid((unsigned)(g.nkc * n), (unsigned)((m->ny + TJ - 1) / TJ), (unsigned)((m->nx + g.ti - 1) / g.ti));
