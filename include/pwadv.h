@@ -377,9 +377,10 @@ pw_status pw_euler_adjoint(const pw_mesh *mesh, const void *u, const void *v, co
 pw_status pw_euler(const pw_mesh *mesh, void *u, void *v, void *w,
                    const void *su, const void *sv, const void *sw, double dt, void *stream);
 
-/* Conservation diagnostics with FP64 accuracy, from a deterministic two-pass
- * tree reduction (the order does not depend on timing: repeated calls give the
- * same bits).  The first pass accumulates double-float sums on the FP32 pipe
+/* Conservation diagnostics with FP64 accuracy, from a deterministic tree
+ * reduction (a fixed grid of blocks whose records the last block to finish
+ * adds in a fixed order: the order does not depend on timing, so repeated
+ * calls give the same bits).  The reduction accumulates double-float sums on the FP32 pipe
  * (each sum within a few units of 2^-46 of the sum of its terms' magnitudes);
  * if an input is outside what that pass carries exactly (a nonzero |x| below
  * 2^-100 or from 2^56 up, NaN, Inf) or a sum of magnitudes is below 2^-40, the
@@ -433,7 +434,7 @@ pw_status pw_residual_ratios(const double *sums, double *out);
  * array is shared by every call: each call rewrites all of it that it reads, so
  * nothing depends on earlier contents, but calls that overlap on the GPU (on
  * different streams or host threads) race on it and must be serialised by the
- * caller.  Copies the weights in, runs the same two-pass FP64 reduction as
+ * caller.  Copies the weights in, runs the same FP64 reduction as
  * pw_residuals on `stream`, copies out and synchronises `stream`. */
 pw_status pw_residuals_noalloc(int nx, int ny, int nz, int nzp, pw_dtype dtype,
                                const double *w_uv, const double *w_w,

@@ -23,7 +23,8 @@ struct pw_mesh {
     double *coef64;          // device, 12*nz: dz zf zn dzn rho_n rho_w tzc1 tzc2 tzd1 tzd2 Wuv Ww
     float *coef32;           // device, 4*nz: tzc1 tzc2 tzd1 tzd2
     float *coefsplit;        // device, 8*(nz+4)+4: float pairs of g, g', r, r' (levels -2..nz+1), tcx, tcy
-    double *partials;        // device, residual scratch: PW_RED_SCRATCH doubles
+    double *partials;        // device, residual scratch: PW_RED_SCRATCH doubles (zeroed at creation)
+    double *host_sums;       // pinned host, PW_RED_STRIDE doubles: where the totals land
     int *status;             // device: [0] timeout status (0 or PW_ERR_TIMEOUT), [1] lid flag,
                              // [2] split-range flag, [3] unused
     int tile_j, tile_i;      // stencil tile: rows per CTA, columns marched per CTA
@@ -37,11 +38,13 @@ struct pw_mesh {
 // reduction geometry of pw_residuals (fixed so the order of sums is fixed):
 // PW_RED_BLOCKS blocks each write PW_RED_STRIDE doubles (the 12 sums and a
 // count of values outside the fast path's range), then PW_RED_STRIDE totals
+// (written by the last block to finish), then one word counting the finished
+// blocks (0 between calls)
 #define PW_RED_BLOCKS 592
 #define PW_RED_THREADS 256
 #define PW_RED_FAST_THREADS 128
 #define PW_RED_STRIDE 13
-#define PW_RED_SCRATCH ((PW_RED_BLOCKS + 1) * PW_RED_STRIDE)
+#define PW_RED_SCRATCH ((PW_RED_BLOCKS + 1) * PW_RED_STRIDE + 1)
 
 // bounded waits: ~1 s at 2 GHz for a copy the kernel needs; ~50 ms when a
 // kernel that already gave up drains copies still in flight.  On expiry the
@@ -134,12 +137,14 @@ pw_status pw_launch_adjoint_split(const pw_mesh *m, const void *const *in, void 
                                   int beta, int add_y, cudaStream_t st);
 
 // The conservation sums (pw_residuals.cu): the 12 sums into the HOST array
-// out, computed on `st` with `scratch` (PW_RED_SCRATCH device doubles) and the
-// energy weights wuv, ww (device, nz each); synchronises `st`.
+// out, computed on `st` with `scratch` (PW_RED_SCRATCH device doubles whose
+// last word is 0) and the energy weights wuv, ww (device, nz each); the
+// totals are copied through `staging` (PW_RED_STRIDE pinned host doubles, or
+// NULL); synchronises `st`.
 pw_status pw_residuals_run(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
                            const double *ww, const void *u, const void *v, const void *w,
                            const void *su, const void *sv, const void *sw, double *scratch,
-                           double *out, cudaStream_t st);
+                           double *staging, double *out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device helpers

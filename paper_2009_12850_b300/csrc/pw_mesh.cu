@@ -194,6 +194,7 @@ static void pw_mesh_free(pw_mesh *m) {
     cudaFree(m->coef32);
     cudaFree(m->coefsplit);
     cudaFree(m->partials);
+    cudaFreeHost(m->host_sums);
     cudaFree(m->status);
     free(m);
 }
@@ -257,6 +258,8 @@ extern "C" pw_status pw_mesh_create(const pw_mesh_desc *d, void *stream, pw_mesh
         (e = cudaMalloc(&m->coef32, 4 * (size_t)nz * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&m->coefsplit, (8 * ((size_t)nz + 4) + 4) * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&m->partials, PW_RED_SCRATCH * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemset(m->partials, 0, PW_RED_SCRATCH * sizeof(double))) != cudaSuccess ||
+        (e = cudaHostAlloc(&m->host_sums, PW_RED_STRIDE * sizeof(double), cudaHostAllocDefault)) != cudaSuccess ||
         (e = cudaMalloc(&m->status, PW_STATUS_WORDS * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&tmp, 3 * (size_t)nz * sizeof(double))) != cudaSuccess) {
         pw_mesh_free(m);

@@ -2,9 +2,10 @@
 // phi in (u, v, w) with source S and energy weight W (rho_n dz on u/v levels,
 // rho_w dzn on w faces, 0 on the lid face),
 //   sum W phi S,  sum W |phi S|,  sum W S,  sum W |S|
-// over the interior, in a deterministic two-pass tree reduction (a fixed grid,
-// a fixed order of terms per thread, a fixed tree), so repeated calls give the
-// same bits.
+// over the interior, in a deterministic tree reduction (a fixed grid, a fixed
+// order of terms per thread, a fixed tree per block, and the block records
+// added in a fixed order by whichever block finishes last), so repeated calls
+// give the same bits.
 //
 // The fast pass keeps FP64 accuracy without the FP64 units (which run at
 // ~1/80 of the FP32 rate on B300): every value is split with integer bit
@@ -106,6 +107,40 @@ __device__ __forceinline__ void pw_res_block_tree(double (&vals)[PW_RED_STRIDE],
     if (threadIdx.x < PW_RED_STRIDE) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
+// After a block's record is written: the last block to finish adds the
+// PW_RED_BLOCKS records (thread t: records t, t + NT, ..., all loads issued
+// before the first add), then the fixed tree, into the totals, and sets the
+// counter back to 0.  Which block is last does not change the order.
+template <int NT>
+__device__ __forceinline__ void pw_res_finish(double *scratch) {
+    constexpr int PER = (PW_RED_BLOCKS + NT - 1) / NT;
+    __shared__ unsigned ticket;
+    __threadfence();  // this block's record is visible before its ticket
+    __syncthreads();
+    unsigned *count = reinterpret_cast<unsigned *>(scratch + PW_RED_SCRATCH - 1);
+    if (threadIdx.x == 0) ticket = atomicAdd(count, 1u);
+    __syncthreads();
+    if (ticket != PW_RED_BLOCKS - 1) return;
+    __threadfence();
+    double r[PER][PW_RED_STRIDE];
+#pragma unroll
+    for (int m = 0; m < PER; m++) {
+        const int b = (int)threadIdx.x + m * NT;
+#pragma unroll
+        for (int q = 0; q < PW_RED_STRIDE; q++) r[m][q] = b < PW_RED_BLOCKS ? __ldcg(scratch + (size_t)b * PW_RED_STRIDE + q) : 0.0;
+    }
+    double vals[PW_RED_STRIDE];
+#pragma unroll
+    for (int q = 0; q < PW_RED_STRIDE; q++) {
+        double a = r[0][q];
+#pragma unroll
+        for (int m = 1; m < PER; m++) a += r[m][q];
+        vals[q] = a;
+    }
+    pw_res_block_tree<NT>(vals, scratch + PW_RED_BLOCKS * PW_RED_STRIDE);
+    if (threadIdx.x == 0) *count = 0u;
+}
+
 template <typename TF, typename TS>
 __global__ void __launch_bounds__(PW_RED_FAST_THREADS)
 pw_residual_fast(const TF *u, const TF *v, const TF *w, const TS *su, const TS *sv, const TS *sw,
@@ -181,6 +216,7 @@ pw_residual_fast(const TF *u, const TF *v, const TF *w, const TS *su, const TS *
     }
     vals[12] = bad ? 1.0 : 0.0;
     pw_res_block_tree<PW_RED_FAST_THREADS>(vals, partials + (size_t)blockIdx.x * PW_RED_STRIDE);
+    pw_res_finish<PW_RED_FAST_THREADS>(partials);
 }
 
 // The plain FP64 pass (used when the fast pass met values outside its range).
@@ -216,25 +252,13 @@ pw_residual_exact(const TF *u, const TF *v, const TF *w, const TS *su, const TS 
         }
     }
     pw_res_block_tree<PW_RED_THREADS>(acc, partials + (size_t)blockIdx.x * PW_RED_STRIDE);
-}
-
-// second pass: the PW_RED_BLOCKS partial records into PW_RED_STRIDE totals
-__global__ void __launch_bounds__(PW_RED_THREADS)
-pw_residual_pass2(const double *partials, int nblocks, double *out) {
-    double vals[PW_RED_STRIDE];
-    for (int q = 0; q < PW_RED_STRIDE; q++) {
-        double a = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partials[(int64_t)b * PW_RED_STRIDE + q];
-        vals[q] = a;
-    }
-    pw_res_block_tree<PW_RED_THREADS>(vals, out);
+    pw_res_finish<PW_RED_THREADS>(partials);
 }
 
 static pw_status pw_residual_launch(bool exact, int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
                                     const double *ww, const void *u, const void *v, const void *w,
                                     const void *su, const void *sv, const void *sw, double *scratch,
                                     cudaStream_t st) {
-    double *totals = scratch + PW_RED_BLOCKS * PW_RED_STRIDE;
 #define PW_RES(TF, TS)                                                                                     \
     do {                                                                                                   \
         if (exact)                                                                                         \
@@ -252,21 +276,21 @@ static pw_status pw_residual_launch(bool exact, int nx, int ny, int nz, int nzp,
     else PW_RES(__nv_bfloat16, float);
 #undef PW_RES
     PW_CUDA(cudaGetLastError());
-    pw_residual_pass2<<<1, PW_RED_THREADS, 0, st>>>(scratch, PW_RED_BLOCKS, totals);
-    PW_CUDA(cudaGetLastError());
     return PW_OK;
 }
 
 pw_status pw_residuals_run(int nx, int ny, int nz, int nzp, pw_dtype dtype, const double *wuv,
                            const double *ww, const void *u, const void *v, const void *w,
                            const void *su, const void *sv, const void *sw, double *scratch,
-                           double *out, cudaStream_t st) {
-    double h[PW_RED_STRIDE];
+                           double *staging, double *out, cudaStream_t st) {
+    double local[PW_RED_STRIDE];
+    double *h = staging ? staging : local;
     for (int pass = 0; pass < 2; pass++) {
         pw_status s = pw_residual_launch(pass == 1, nx, ny, nz, nzp, dtype, wuv, ww, u, v, w, su, sv, sw,
                                          scratch, st);
         if (s != PW_OK) return s;
-        PW_CUDA(cudaMemcpyAsync(h, scratch + PW_RED_BLOCKS * PW_RED_STRIDE, sizeof(h), cudaMemcpyDeviceToHost, st));
+        PW_CUDA(cudaMemcpyAsync(h, scratch + PW_RED_BLOCKS * PW_RED_STRIDE, PW_RED_STRIDE * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
         PW_CUDA(cudaStreamSynchronize(st));
         // the fast pass stands unless it met values outside its range or a sum
         // of magnitudes is so small that underflow of its terms could matter
@@ -288,7 +312,7 @@ extern "C" pw_status pw_residuals(const pw_mesh *m, const void *u, const void *v
     for (int q = 0; q < 6; q++)
         if ((s = pw_check_ptr(ps[q], nm[q])) != PW_OK) return s;
     return pw_residuals_run(m->nx, m->ny, m->nz, m->nzp, m->dtype, m->coef64 + 10 * m->nz, m->coef64 + 11 * m->nz,
-                            u, v, w, su, sv, sw, m->partials, out, (cudaStream_t)stream);
+                            u, v, w, su, sv, sw, m->partials, m->host_sums, out, (cudaStream_t)stream);
 }
 
 extern "C" pw_status pw_residual_ratios(const double *sums, double *out) {

@@ -75,12 +75,13 @@ extern "C" pw_status pw_residuals_noalloc(int nx, int ny, int nz, int nzp, pw_dt
     double *scratch = nullptr;
     pw_status s = pw_noalloc_scratch_ptr(&scratch);
     if (s != PW_OK) return s;
-    // every entry of the reduction records is rewritten by each pass
+    // every entry of the reduction records is rewritten by each pass; the
+    // finished-block counter (zero-initialised) is back at 0 after each
     double *wuv = scratch + PW_RED_SCRATCH, *ww = wuv + PW_NOALLOC_MAX_NZ;
     cudaStream_t st = (cudaStream_t)stream;
     PW_CUDA(cudaMemcpyAsync(wuv, w_uv, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, st));
     PW_CUDA(cudaMemcpyAsync(ww, w_w, (size_t)nz * sizeof(double), cudaMemcpyHostToDevice, st));
-    s = pw_residuals_run(nx, ny, nz, nzp, dtype, wuv, ww, u, v, w, su, sv, sw, scratch, out, st);
+    s = pw_residuals_run(nx, ny, nz, nzp, dtype, wuv, ww, u, v, w, su, sv, sw, scratch, nullptr, out, st);
     if (s != PW_OK) return s;
     return PW_OK;
 }
