@@ -199,7 +199,7 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
         for (int c = 0; c < 4; c++) {
             const float2 x = cpair(a < g.nz ? cz[c * g.nz + a] : 0.0);
             const float2 y = cpair(b < g.nz ? cz[c * g.nz + b] : 0.0);
-            ctab[t * 4 + c] = make_float4(x.x, y.x, x.y, y.y);
+            ctab[c * half + t] = make_float4(x.x, y.x, x.y, y.y);
         }
     }
     if (tid == 0) {
@@ -207,7 +207,9 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
         ctab[half * 4] = make_float4(x.x, x.x, x.y, x.y);
         ctab[half * 4 + 1] = make_float4(y.x, y.x, y.y, y.y);
     }
-    auto coef = [&](int a) { return pw_ldc(ctab, tk * 4 + a); };
+    // coefficient a of level pair t at a * half + t: a warp's 16 level pairs
+    // read 256 contiguous bytes (conflict-free)
+    auto coef = [&](int a) { return pw_ldc(ctab, a * half + tk); };
     auto tcoef = [&](int a) { return pw_ldc(ctab, half * 4 + a); };
     const bool active = j < g.ny;
     const bool oka = ka < g.nz, okz = kz < g.nz;
