@@ -131,6 +131,9 @@ pw_status pw_launch_advect_scalars(const pw_mesh *m, const void *u, const void *
                                    const void *const *phi, void *const *sphi, int beta, cudaStream_t st,
                                    int tile_j, int tile_i, int group);
 pw_status pw_launch_halo(const pw_mesh *m, void *const *f, int nf, cudaStream_t st);
+// ULTIMATE-QUICKEST for FP64 meshes in double-float arithmetic (pw_tvd_split.cu)
+pw_status pw_launch_tvd_split(const pw_mesh *m, const void *u, const void *v, const void *w, int n,
+                              const void *const *phi, void *const *sphi, double dt, int beta, cudaStream_t st);
 // FP64 adjoint in double-float arithmetic (pw_adjoint_split.cu): in = u, v, w,
 // gsu, gsv, gsw (halos of the gradients filled), out = gu, gv, gw.
 pw_status pw_launch_adjoint_split(const pw_mesh *m, const void *const *in, void *const *out, double alpha,

@@ -323,6 +323,7 @@ static pw_status pw_launch_tvd(const pw_mesh *m, const void *u, const void *v, c
     const int ti = m->tile_i;
     switch (m->dtype) {
         case PW_F64:
+            if (m->algo == PW_ALGO_F64_SPLIT) return pw_launch_tvd_split(m, u, v, w, n, phi, sphi, dt, beta, st);
             return pw_launch_tvd_t<double, double, double, 8>(m, u, v, w, n, phi, sphi, dt, beta, st, ti);
         case PW_F32:
             return pw_launch_tvd_t<float, float, float, 8>(m, u, v, w, n, phi, sphi, dt, beta, st, ti);

@@ -36,7 +36,8 @@ def pw():
 
 
 def rounded(arrs, dtype):
-    t = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16, "bf16_out": torch.bfloat16}[dtype]
+    t = {"f64": torch.float64, "f64n": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16,
+         "bf16_out": torch.bfloat16}[dtype]
     return [torch.from_numpy(np.ascontiguousarray(a)).to(t).to(torch.float64).numpy() for a in arrs]
 
 
@@ -54,8 +55,15 @@ def run_tvd(m, wind, phis, dt, beta=0, init=None):
     return [m.interior(s).double().cpu().numpy() for s in S]
 
 
+def mesh(pw, nx, ny, nz, dx, dy=None, dtype="f64"):
+    """dtype "f64" is the double-float kernel (the FP64 default), "f64n" native FP64."""
+    if dtype == "f64n":
+        return pw.Mesh(nx, ny, nz, dx, dy if dy is not None else dx, dtype="f64", algo="native")
+    return pw.Mesh(nx, ny, nz, dx, dy if dy is not None else dx, dtype=dtype)
+
+
 def tolerances(dtype):
-    if dtype == "f64":
+    if dtype in ("f64", "f64n"):
         return TOL_F64, TOL_F64
     if dtype == "bf16_out":   # the bfloat16 output alone rounds by up to 2^-8 of |s|
         return 2.0 ** -7, TOL_TVD_BF16_OUT
@@ -64,7 +72,7 @@ def tolerances(dtype):
 
 SHAPES = [(64, 64, 64), (37, 23, 13), (5, 7, 1), (1, 9, 6), (9, 1, 5), (3, 3, 2), (50, 17, 130),
           (16, 24, 300), (2, 2, 33)]
-DTYPES = ["f64", "f32", "bf16", "bf16_out"]
+DTYPES = ["f64", "f64n", "f32", "bf16", "bf16_out"]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -74,7 +82,7 @@ def test_tvd_matches_oracle(pw, shape, dtype, dt):
     # dt = 2 s: Courant numbers around 0.2 (dx 50 m, winds 5 +- 1 m/s);
     # dt = 9 s: around 0.9, some above 1 (the limiter's window closes there)
     nx, ny, nz = shape
-    m = pw.Mesh(nx, ny, nz, 50.0, 35.0, dtype=dtype)
+    m = mesh(pw, nx, ny, nz, 50.0, 35.0, dtype=dtype)
     wind = rounded(synthetic.wind_fields(nx, ny, nz, 21), dtype)
     phis = rounded(synthetic.scalar_fields(nx, ny, nz, 2, 22), dtype)
     got = run_tvd(m, wind, phis, dt)
@@ -85,7 +93,7 @@ def test_tvd_matches_oracle(pw, shape, dtype, dt):
         compare(f"s{q}", got[q], ref, cond, tn, tc)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32"])
 def test_tvd_steep_and_signed_data(pw, dtype):
     """Fronts, plateaus, extrema and sign changes (every branch of the limiter:
     exact ties between neighbours, monotone runs where the Courant bound acts,
@@ -99,7 +107,7 @@ def test_tvd_steep_and_signed_data(pw, dtype):
     phi = np.where(rng.random((nx, ny, nz)) < 0.5, 1.0, 0.0) + np.round(rng.standard_normal((nx, ny, nz)), 1)
     phi[:, :, 10:20] = 2.5  # a plateau: ties between neighbours
     wind, phis = rounded([u, v, w], dtype), rounded([phi], dtype)
-    m = pw.Mesh(nx, ny, nz, 40.0, dtype=dtype)
+    m = mesh(pw, nx, ny, nz, 40.0, dtype=dtype)
     c = oracle.Coeffs(nz, 40.0, 40.0)
     tn, tc = tolerances(dtype)
     for dt in (1.0, 4.0, 12.0):
@@ -109,12 +117,12 @@ def test_tvd_steep_and_signed_data(pw, dtype):
 
 
 @pytest.mark.parametrize("n", [1, 3, 16])
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32"])
 def test_tvd_counts_are_independent(pw, n, dtype):
     """n scalars in one call equal n calls of one scalar, bit for bit, and match
     the oracle."""
     nx, ny, nz = 21, 34, 70
-    m = pw.Mesh(nx, ny, nz, 40.0, dtype=dtype)
+    m = mesh(pw, nx, ny, nz, 40.0, dtype=dtype)
     wind = rounded(synthetic.wind_fields(nx, ny, nz, 24), dtype)
     phis = rounded(synthetic.scalar_fields(nx, ny, nz, n, 25), dtype)
     together = run_tvd(m, wind, phis, 3.0)
@@ -128,9 +136,10 @@ def test_tvd_counts_are_independent(pw, n, dtype):
 
 
 @pytest.mark.parametrize("tile_i", [1, 4, 7, 64, 300])
-def test_tvd_tiles_do_not_change_results(pw, tile_i):
+@pytest.mark.parametrize("dtype", ["f64", "f64n"])
+def test_tvd_tiles_do_not_change_results(pw, tile_i, dtype):
     nx, ny, nz = 45, 29, 40
-    m = pw.Mesh(nx, ny, nz, 50.0, dtype="f64")
+    m = mesh(pw, nx, ny, nz, 50.0, dtype=dtype)
     wind = synthetic.wind_fields(nx, ny, nz, 26)
     phis = synthetic.scalar_fields(nx, ny, nz, 2, 27)
     base = run_tvd(m, wind, phis, 5.0)
@@ -143,7 +152,7 @@ def test_tvd_tiles_do_not_change_results(pw, tile_i):
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_tvd_accumulate(pw, dtype):
     nx, ny, nz = 19, 22, 17
-    m = pw.Mesh(nx, ny, nz, 30.0, dtype=dtype)
+    m = mesh(pw, nx, ny, nz, 30.0, dtype=dtype)
     wind = rounded(synthetic.wind_fields(nx, ny, nz, 28), dtype)
     phis = rounded(synthetic.scalar_fields(nx, ny, nz, 2, 29), dtype)
     rng = np.random.default_rng(30)
@@ -158,13 +167,14 @@ def test_tvd_accumulate(pw, dtype):
             # once (2^-8 of the sum); f itself is that source rounded (2^-8 of |f|)
             assert np.all(np.abs(a - (i + f)) <= 2.0 ** -8 * (np.abs(i + f) + 2 * np.abs(f)))
         else:
-            tol = 1e-15 if dtype == "f64" else 2.0 ** -23
+            tol = 1e-15 if dtype in ("f64", "f64n") else 2.0 ** -23
             assert np.allclose(a, i + f, rtol=tol, atol=tol * np.abs(i + f).max())
 
 
-def test_tvd_lid_and_halos_untouched(pw):
+@pytest.mark.parametrize("dtype", ["f64", "f64n"])
+def test_tvd_lid_and_halos_untouched(pw, dtype):
     nx, ny, nz = 13, 11, 9
-    m = pw.Mesh(nx, ny, nz, 30.0, dtype="f64")
+    m = mesh(pw, nx, ny, nz, 30.0, dtype=dtype)
     u, v, w = synthetic.wind_fields(nx, ny, nz, 31)
     phi = synthetic.scalar_fields(nx, ny, nz, 1, 32)[0]
     base = run_tvd(m, [u, v, w], [phi], 2.0)[0]
@@ -183,7 +193,7 @@ def test_tvd_lid_and_halos_untouched(pw):
     assert torch.all(S[mask] == 123.0)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32"])
 def test_tvd_properties_on_device(pw, dtype):
     """What the scheme guarantees, checked on the device results at a size past
     a few tiles: one-dimensional uniform flow with c <= 1 keeps every value in
@@ -191,7 +201,7 @@ def test_tvd_properties_on_device(pw, dtype):
     Courant number 1 is an exact shift; a constant field stays constant under a
     divergence-free (uniform) wind."""
     nx, ny, nz = 200, 3, 2
-    m = pw.Mesh(nx, ny, nz, 10.0, dtype=dtype)
+    m = mesh(pw, nx, ny, nz, 10.0, dtype=dtype)
     rng = np.random.default_rng(33)
     line = np.where(np.arange(nx) % 23 < 9, 1.0, 0.0) + 0.1 * rng.random(nx)
     phi = rounded([np.broadcast_to(line[:, None, None], (nx, ny, nz)).copy()], dtype)[0]
@@ -201,14 +211,14 @@ def test_tvd_properties_on_device(pw, dtype):
             dt = cr * 10.0 / abs(U)
             s = run_tvd(m, [zero + U, zero, zero], [phi], dt)[0]
             new = phi + dt * s
-            tol = 1e-13 if dtype == "f64" else 1e-5
+            tol = 1e-13 if dtype in ("f64", "f64n") else 1e-5
             assert new.max() <= phi.max() + tol and new.min() >= phi.min() - tol
             tv = lambda a: np.abs(np.diff(np.r_[a, a[:1]])).sum()
             assert tv(new[:, 1, 0]) <= tv(phi[:, 1, 0]) * (1 + tol)
             if cr == 1.0:
                 np.testing.assert_allclose(new, np.roll(phi, 1 if U > 0 else -1, axis=0), atol=tol)
     s = run_tvd(m, [zero + 3.0, zero - 2.0, zero], [zero + 4.5], 2.0)[0]
-    assert np.abs(s).max() <= (1e-15 if dtype == "f64" else 1e-6)
+    assert np.abs(s).max() <= (1e-15 if dtype in ("f64", "f64n") else 1e-6)
 
 
 def test_tvd_argument_errors(pw):
@@ -232,13 +242,13 @@ def test_tvd_argument_errors(pw):
     assert m.device_status() == 0
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32"])
 def test_tvd_full_size_every_point(pw, dtype):
     """θ on the 1024x1024x128 bandwidth workload (dx 25 m, dt 2 s) in the
     launch configuration the benchmark times: every point against the oracle."""
     nx, ny, nz = 1024, 1024, 128
     dt = 2.0
-    m = pw.Mesh(nx, ny, nz, 25.0, dtype=dtype)
+    m = mesh(pw, nx, ny, nz, 25.0, dtype=dtype)
     wind = rounded(synthetic.wind_fields(nx, ny, nz, 1234 + 1), dtype)
     phi = rounded([synthetic.scalar_fields(nx, ny, nz, 1, 1234 + 101)[0]], dtype)[0]
     got = run_tvd(m, wind, [phi], dt)[0]
@@ -246,3 +256,37 @@ def test_tvd_full_size_every_point(pw, dtype):
     ref, cond = oracle.advect_tvd(c, *wind, phi, dt, want_cond=True)
     tn, tc = tolerances(dtype)
     compare_slabs("theta", got, ref, cond, tn, tc)
+
+
+def test_tvd_split_range_is_reported(pw):
+    """The double-float kernel reads values outside its range as 0 and says so
+    in the mesh status word; native FP64 has no such limit."""
+    from paper_2009_12850_b300 import _lib as L
+    nx, ny, nz = 12, 10, 9
+    u, v, w = synthetic.wind_fields(nx, ny, nz, 36)
+    phi = synthetic.scalar_fields(nx, ny, nz, 1, 37)[0]
+    m = mesh(pw, nx, ny, nz, 30.0, dtype="f64")
+    # in range: no report
+    run_tvd(m, [u, v, w], [phi], 2.0)
+    for bad in (float("nan"), float("inf"), 2.0 ** 61):
+        p2 = phi.copy()
+        p2[3, 4, 5] = bad
+        U = [m.from_interior(a) for a in (u, v, w)]
+        S = m.empty_out()
+        m.advect_tvd(*U, [m.from_interior(p2)], 2.0, [S])
+        torch.cuda.synchronize()
+        assert m.device_status() == L.PW_ERR_RANGE
+    u2 = u.copy()
+    u2[1, 1, 1] = 2.0 ** 41
+    U = [m.from_interior(a) for a in (u2, v, w)]
+    S = m.empty_out()
+    m.advect_tvd(*U, [m.from_interior(phi)], 2.0, [S])
+    torch.cuda.synchronize()
+    assert m.device_status() == L.PW_ERR_RANGE
+    # native FP64 takes the large value as it is
+    mn = mesh(pw, nx, ny, nz, 30.0, dtype="f64n")
+    p2 = phi.copy()
+    p2[3, 4, 5] = 2.0 ** 61
+    got = run_tvd(mn, [u, v, w], [p2], 2.0)[0]
+    ref, cond = oracle.advect_tvd(oracle.Coeffs(nz, 30.0, 30.0), u, v, w, p2, 2.0, want_cond=True)
+    compare("native", got, ref, cond, TOL_F64, TOL_F64)
