@@ -91,10 +91,14 @@ __device__ __forceinline__ DF dfs_div(DF n, DF d) {
 }
 __device__ __forceinline__ DF dfs_sel(bool c, DF a, DF b) { return DF{c ? a.h : b.h, c ? a.l : b.l}; }
 
-// sign of a double from its bits: -1, 0 or +1 (-0 counts as 0)
+// sign of a double from its bits: -1, 0 or +1 (-0 counts as 0).  The words
+// are taken through an opaque move so that the test stays on the integer
+// units: written as a comparison of the double, it runs on the FP64 pipe,
+// which then bounds the whole kernel.
 __device__ __forceinline__ int pw_dsign(double x) {
-    const long long b = __double_as_longlong(x);
-    return (b << 1) == 0 ? 0 : (b < 0 ? -1 : 1);
+    uint32_t lo, hi;
+    asm volatile("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+    return ((hi << 1) | lo) == 0u ? 0 : ((int)hi < 0 ? -1 : 1);
 }
 
 // a double split into a 2^8-scaled double-float (range flag into `bad`)
@@ -119,7 +123,8 @@ __device__ __forceinline__ DF pw_tvds_flux(double a, DF cfp, DF cfn, double pl2,
     const DF P = pw_dsplit(pc, PW_SPLIT_SCALAR_EHI, bad);
     const DF D0 = pw_dsplit(d0, PW_SPLIT_SCALAR_EHI, bad);
     const DF D1 = pw_dsplit(d1, PW_SPLIT_SCALAR_EHI, bad);
-    const DF c = dfs_mul(pos ? A : dfs_neg(A), pos ? cfp : cfn);  // unscaled
+    // the two parts of a split value carry its sign, so |x| is |h| + |l|
+    const DF c = dfs_mul(DF{fabsf(A.h), fabsf(A.l)}, pos ? cfp : cfn);  // unscaled
     constexpr float six_h = (float)(1.0 / 6.0), six_l = (float)(1.0 / 6.0 - (double)six_h);
     const DF one{1.0f, 0.0f}, sixth{six_h, six_l};  // 1/6 as h + l (folded by the compiler)
     const DF w1 = dfs_sub(one, c);
@@ -127,7 +132,7 @@ __device__ __forceinline__ DF pw_tvds_flux(double a, DF cfp, DF cfn, double pl2,
     const DF inner = dfs_sub(DF{0.5f * D1.h, 0.5f * D1.l}, dfs_mul(k6, dfs_sub(D1, D0)));
     const DF tq = dfs_mul(w1, inner);  // q - phi_C
     const DF w = dfs_val(w1) > 0.0f ? w1 : DF{0.0f, 0.0f};
-    const DF aD1 = s1 < 0 ? dfs_neg(D1) : D1, aD0 = s0 < 0 ? dfs_neg(D0) : D0;
+    const DF aD1{fabsf(D1.h), fabsf(D1.l)}, aD0{fabsf(D0.h), fabsf(D0.l)};
     const bool nearD = dfs_val(dfs_sub(dfs_mul(c, aD1), dfs_mul(aD0, w))) < 0.0f;
     // the window's end nearer 0 (the quotient is only taken when c > 0)
     const DF B = nearD ? D1 : dfs_div(dfs_mul(D0, w), c);
