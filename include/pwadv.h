@@ -281,8 +281,12 @@ pw_status pw_advect_scalars_step(const pw_mesh *mesh, const void *u, const void 
  * along x and y).  phi and sphi are HOST arrays of n device pointers
  * (1 <= n <= PW_MAX_SCALARS) in the mesh layout; sphi[a] has the source type
  * of the mesh dtype (binary64 for PW_F64, bfloat16 for PW_BF16_OUT, binary32
- * otherwise); beta as in pw_advect.  Arithmetic: native FP64 for PW_F64 (both
- * algorithms), FP32 otherwise.  No output may alias an input or another
+ * otherwise); beta as in pw_advect.  Arithmetic: for PW_F64, double-float on
+ * the FP32 pipe (PW_ALGO_F64_SPLIT, the default: the direction and
+ * monotonicity decisions on exact FP64 differences, the rest within a few
+ * units of 2^-46 of |a| (|phi_U| + |phi_C| + |phi_D|) per face; the range
+ * contract of PW_ALGO_F64_SPLIT, out-of-range values setting PW_ERR_RANGE in
+ * the mesh status) or native FP64 (PW_ALGO_F64_NATIVE); FP32 otherwise.  No output may alias an input or another
  * output.  Returns PW_ERR_ARG for bad arguments; timeouts as pw_advect. */
 pw_status pw_advect_tvd(const pw_mesh *mesh, const void *u, const void *v, const void *w, int n,
                         const void *const *phi, void *const *sphi, double dt, int beta, void *stream);
