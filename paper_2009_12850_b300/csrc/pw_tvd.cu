@@ -21,11 +21,13 @@
 // Layout of the work: an x-march over TMA-staged (j,k) planes of u, v, w and
 // phi (rows j0-2 .. j0+TJ+1 and a 16-byte k halo: the scheme reaches two cells
 // in x, y and z; the mesh's halos are two wide).  A CTA owns TJ rows x 32
-// levels, one level per thread.  Each step takes the newest plane p (column
+// levels, two consecutive levels per thread (the march's per-step work is
+// paid once per two values).  Each step takes the newest plane p (column
 // i0-2+p) and
 //   1. evaluates the y and z face fluxes of that plane: each thread the faces
-//      south of and below its point, warps 0 and 1 also the faces north of the
-//      last row and above the top level, into one of two shared-memory sets;
+//      south of and below its two points, row 0's threads also the faces north
+//      of the last row, TJ threads of row 1 those above the top level, into one
+//      of two shared-memory sets;
 //   2. after the step's one CTA barrier (which also frees plane p's ring slot
 //      for plane p + NS), forms each point's y + z flux divergence D (held two
 //      steps in registers);
@@ -37,7 +39,7 @@
 
 #include "pw_march.cuh"
 
-#define PW_TVD_NS 4   // ring slots (three planes of look-ahead)
+#define PW_TVD_NS 3   // ring slots (two planes of look-ahead)
 #define PW_TVD_KC 32  // levels per CTA (one warp per row)
 
 struct PwTvdGeom {
@@ -93,21 +95,67 @@ __device__ __forceinline__ TC pw_tvd_flux(TC a, TC cfp, TC cfn, TC pl2, TC pl, T
     return a * f;
 }
 
-// TJ rows per CTA, TS storage, TC arithmetic, TO source type.
+// two consecutive values (levels k, k+1; k even, so the pair is aligned) of a
+// staged row, widened to the compute type
+template <typename TS, typename TC>
+__device__ __forceinline__ void pw_tvd_ld2(const TS *p, TC &a, TC &b) {
+    if constexpr (std::is_same<TS, float>::value) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        a = v.x;
+        b = v.y;
+    } else if constexpr (std::is_same<TS, double>::value) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        a = (TC)v.x;
+        b = (TC)v.y;
+    } else {
+        const uint32_t v = *reinterpret_cast<const uint32_t *>(p);
+        a = __uint_as_float(v << 16);  // bf16 -> f32 is exact
+        b = __uint_as_float(v & 0xffff0000u);
+    }
+}
+
+// the two results of a thread (levels k, k+1; the second only when k+1 < nz)
+template <typename TO, typename TC>
+__device__ __forceinline__ void pw_tvd_st2(TO *o, TC s0, TC s1, bool two, int beta) {
+    if constexpr (std::is_same<TO, __nv_bfloat16>::value) {
+        const float a = beta ? __bfloat162float(o[0]) + (float)s0 : (float)s0;
+        if (two) {
+            const float b = beta ? __bfloat162float(o[1]) + (float)s1 : (float)s1;
+            *reinterpret_cast<__nv_bfloat162 *>(o) = __floats2bfloat162_rn(a, b);
+        } else {
+            o[0] = __float2bfloat16_rn(a);
+        }
+    } else {
+        using V = typename std::conditional<sizeof(TO) == 8, double2, float2>::type;
+        if (two) {
+            V v = *reinterpret_cast<const V *>(o);
+            v.x = beta ? v.x + (TO)s0 : (TO)s0;
+            v.y = beta ? v.y + (TO)s1 : (TO)s1;
+            *reinterpret_cast<V *>(o) = v;
+        } else {
+            o[0] = beta ? o[0] + (TO)s0 : (TO)s0;
+        }
+    }
+}
+
+// TJ rows per CTA, TS storage, TC arithmetic, TO source type.  A thread owns
+// two levels (k, k+1) of one row; 16 threads cover a row's 32 levels.
 //
-// Face schedule of a step, per thread (tr, tl) = (row, level in the chunk):
-//   A: the y face south of its point (rows j-1 | j),
-//   B: the z face below its point (levels k-1 | k),
-//   C: warp 0 takes the y faces north of the last row, lanes 0..TJ-1 of warp 1
-//      the z faces above the chunk's top level;
-// a thread keeps its own A and B fluxes and reads the north and upper ones
-// from shared memory after the step's barrier.
+// Face schedule of a step, per thread (tr, t), k = k0 + 2t:
+//   A: the y faces south of its two points (rows j-1 | j),
+//   B: the z faces below its two points (levels k-1 | k and k | k+1),
+//   C: row 0's threads also take the y faces north of the last row, the
+//      first TJ threads of row 1 the z face above the chunk's top level of
+//      row r = tid - 16;
+// the face above level k is the thread's own second B face; those north of
+// its points and above level k+1 are read from shared memory after the
+// step's barrier.
 template <typename TS, typename TC, typename TO, int TJ>
-__global__ void __launch_bounds__(TJ * PW_TVD_KC)
+__global__ void __launch_bounds__(TJ * PW_TVD_KC / 2)
 pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
              const __grid_constant__ CUtensorMap mw, const __grid_constant__ PwTvdSet set,
              const double *__restrict__ coef64, const PwTvdGeom g, int beta, int *__restrict__ status) {
-    constexpr int KC = PW_TVD_KC, NS = PW_TVD_NS, ROWS = TJ + 4;
+    constexpr int KC = PW_TVD_KC, NS = PW_TVD_NS, ROWS = TJ + 4, HK = KC / 2;
     using SH = PwTvdShape<TS, TJ>;
     constexpr int H = SH::H, KB = SH::KB, FS = SH::FS;
     constexpr int NGY = (TJ + 1) * KC, NGZ = TJ * (KC + 1);
@@ -117,12 +165,14 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
     const int j0 = blockIdx.y * TJ, i0 = blockIdx.z * g.ti, k0 = kchunk * KC;
     TS *planes = reinterpret_cast<TS *>(smem_raw);
     TC *Gbuf = reinterpret_cast<TC *>(smem_raw + (size_t)NS * 4 * FS * sizeof(TS));  // two sets of faces
-    uint64_t *bars = reinterpret_cast<uint64_t *>(Gbuf + 2 * (NGY + NGZ));
+    TC *cft = Gbuf + 2 * (NGY + NGZ);  // dt / dz(K) for K = k0-1 .. k0+KC (0 outside the column)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(cft) +
+                                                  ((KC + 2) * sizeof(TC) + 15) / 16 * 16);
 
-    const int tid = threadIdx.x;
-    const int tr = tid / KC, tl = tid % KC;
-    const int j = j0 + tr, k = k0 + tl;
-    const bool active = j < g.ny && k < g.nz;
+    const int tid = threadIdx.x, nt = TJ * HK;
+    const int tr = tid / HK, t = tid % HK;
+    const int j = j0 + tr, k = k0 + 2 * t;
+    const bool act0 = j < g.ny && k < g.nz, two = k + 1 < g.nz;
     const int i_end = min(i0 + g.ti, g.nx);
     const int nplanes = i_end - i0 + 4;
     constexpr uint32_t slot_bytes = 4u * ROWS * KB * sizeof(TS);
@@ -134,6 +184,10 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
         pw_prefetch_map(&set.phi[sc]);
         for (int s = 0; s < NS; s++) pw_mbar_init(&bars[s], 1);
         pw_fence_barrier_init();
+    }
+    for (int q = tid; q < KC + 2; q += nt) {
+        const int K = k0 - 1 + q;
+        cft[q] = (K >= 0 && K < g.nz) ? (TC)(g.dt / coef64[K]) : TC(0);
     }
     __syncthreads();
 
@@ -160,34 +214,36 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
             atomicExch(status, (int)PW_ERR_TIMEOUT);
         }
     };
-    auto dtdz = [&](int K) { return (K >= 0 && K < g.nz) ? (TC)(g.dt / coef64[K]) : TC(0); };
 
     const TC cfx = (TC)g.dtdx, cfy = (TC)g.dtdy, rdx = (TC)g.rdx, rdy = (TC)g.rdy;
-    const TC fz1 = (k > 0 && k < g.nz) ? (TC)(4.0 * coef64[6 * g.nz + k]) : TC(0);
-    const TC fz2 = (k < g.nz - 1) ? (TC)(4.0 * coef64[7 * g.nz + k]) : TC(0);
-    // B: the face below level k (K = k-1): exists for 1 <= k <= nz-1
-    const bool zB = k >= 1 && k < g.nz;
-    const TC cfBp = dtdz(k - 1), cfBn = dtdz(k);
-    const bool farBp = k >= 2, farBn = k + 1 < g.nz;
-    // C: warp 0: the y face north of row TJ-1; warp 1, lane r < TJ: the z face
-    // above level k0+KC-1 of row r
-    const int roleC = tid < KC ? 1 : (tid < KC + TJ ? 2 : 0);
-    const int rC = tid - KC;  // row of a role-2 thread
+    TC fz1[2], fz2[2];
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+        const int kk = k + m;
+        fz1[m] = (kk > 0 && kk < g.nz) ? (TC)(4.0 * coef64[6 * g.nz + kk]) : TC(0);
+        fz2[m] = (kk < g.nz - 1) ? (TC)(4.0 * coef64[7 * g.nz + kk]) : TC(0);
+    }
+    // B faces: below level k (K = k-1) and below level k+1 (K = k)
+    const bool zB0 = k >= 1 && k < g.nz, zB1 = k + 1 < g.nz;
+    const TC cfm = cft[2 * t], cf0 = cft[2 * t + 1], cf1 = cft[2 * t + 2];  // dt/dz(k-1), (k), (k+1)
+    // C: row 0's threads: the y faces north of row TJ-1 at levels k, k+1;
+    // threads HK .. HK+TJ-1: the z face above level k0+KC-1 of row tid-HK
+    const int roleC = tid < HK ? 1 : (tid < HK + TJ ? 2 : 0);
+    const int rC = tid - HK;
     const int KT = k0 + KC - 1;
     const bool zC = KT < g.nz - 1;
-    const TC cfCp = dtdz(KT), cfCn = dtdz(KT + 1);
+    const TC cfCp = cft[KC], cfCn = cft[KC + 1];
     const bool farCn = KT + 2 < g.nz;
 
-    const int oA = tr * KB + H + tl;             // A: phi rows j-2 .. j+1, v(j-1) one row down
-    const int oB = (tr + 2) * KB + H + tl - 2;   // B: levels k-2 .. k+1 of row j; w(k-1)
-    const int own = (tr + 2) * KB + H + tl;      // this thread's (j, k)
-    const int oC = roleC == 1 ? TJ * KB + H + tl : (rC + 2) * KB + H + KC - 2;
+    const int oA = tr * KB + H + 2 * t;            // A: phi rows j-2 .. j+1 at (k, k+1), v(j-1) one row down
+    const int oB = (tr + 2) * KB + H + 2 * t - 2;  // B: pairs (k-2, k-1), (k, k+1), (k+2, k+3) of row j
+    const int own = (tr + 2) * KB + H + 2 * t;     // this thread's (j, k)
+    const int oC = roleC == 1 ? TJ * KB + H + 2 * t : (rC + 2) * KB + H + KC - 2;
 
-    TO *out = reinterpret_cast<TO *>(set.out[sc]);
-    TC ph[4] = {TC(0), TC(0), TC(0), TC(0)};  // phi at columns c-1 .. c+2 (own point)
-    TC uw[3] = {TC(0), TC(0), TC(0)};         // u at columns c .. c+2
-    TC D1 = TC(0), D2 = TC(0);                // y + z divergence of columns p-1, p-2
-    TC Gx_w = TC(0);                          // x flux on the west face of the column written next
+    TO *o = reinterpret_cast<TO *>(set.out[sc]) + (long long)(i0 + 2) * g.si + (long long)(j + 2) * g.sj + k;
+    TC ph[4][2] = {}, uw[3][2] = {};  // phi at columns c-1 .. c+2, u at c .. c+2 (own points)
+    TC D1[2] = {}, D2[2] = {};        // y + z divergence of columns p-1, p-2
+    TC Gx_w[2] = {};                  // x flux on the west face of the column written next
 
     for (int p = 0; p < nplanes; p++) {
         // every thread waits for plane p itself; the step's one CTA barrier
@@ -197,35 +253,64 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
         const TS *P = slot(p);
         const TS *Pu = P, *Pv = P + FS, *Pw = P + 2 * FS, *Pp = P + 3 * FS;
         const bool faces = p >= 2 && p < nplanes - 2;  // columns i0 .. i_end-1
-        const TC pC = pw_to<TC>(Pp[own]);
-        TC GA = TC(0), GB = TC(0);
+        TC c0v, c1v;  // phi at (k, k+1)
+        pw_tvd_ld2<TS, TC>(Pp + own, c0v, c1v);
+        TC GA[2] = {}, GB[2] = {};
         if (faces) {
-            GA = pw_tvd_flux<TC>(pw_to<TC>(Pv[oA + KB]), cfy, cfy, pw_to<TC>(Pp[oA]), pw_to<TC>(Pp[oA + KB]), pC,
-                                 pw_to<TC>(Pp[oA + 3 * KB]), true, true);
-            if (zB)
-                GB = pw_tvd_flux<TC>(pw_to<TC>(Pw[oB + 1]), cfBp, cfBn, pw_to<TC>(Pp[oB]), pw_to<TC>(Pp[oB + 1]),
-                                     pC, pw_to<TC>(Pp[oB + 3]), farBp, farBn);
+            TC s0, s1, r0, r1, n0, n1, v0, v1;
+            pw_tvd_ld2<TS, TC>(Pp + oA, s0, s1);
+            pw_tvd_ld2<TS, TC>(Pp + oA + KB, r0, r1);
+            pw_tvd_ld2<TS, TC>(Pp + oA + 3 * KB, n0, n1);
+            pw_tvd_ld2<TS, TC>(Pv + oA + KB, v0, v1);
+            GA[0] = pw_tvd_flux<TC>(v0, cfy, cfy, s0, r0, c0v, n0, true, true);
+            GA[1] = pw_tvd_flux<TC>(v1, cfy, cfy, s1, r1, c1v, n1, true, true);
+            TC m2, m1, p2, p3, wm, wq, w0, w1;
+            pw_tvd_ld2<TS, TC>(Pp + oB, m2, m1);
+            pw_tvd_ld2<TS, TC>(Pp + oB + 4, p2, p3);
+            pw_tvd_ld2<TS, TC>(Pw + oB, wq, wm);  // w(k-2), w(k-1)
+            pw_tvd_ld2<TS, TC>(Pw + oB + 2, w0, w1);
+            // every staged value is finite (levels outside the column arrive
+            // as 0), so faces below level 0 or past the lid are formed and dropped
+            const TC b0 = pw_tvd_flux<TC>(wm, cfm, cf0, m2, m1, c0v, c1v, k >= 2, k + 1 < g.nz);
+            const TC b1 = pw_tvd_flux<TC>(w0, cf0, cf1, m1, c0v, c1v, p2, k >= 1, k + 2 < g.nz);
+            GB[0] = zB0 ? b0 : TC(0);
+            GB[1] = zB1 ? b1 : TC(0);
+            (void)wq;
+            (void)w1;
+            (void)p3;
             if (roleC == 1) {
-                Gy[TJ * KC + tl] = pw_tvd_flux<TC>(pw_to<TC>(Pv[oC + KB]), cfy, cfy, pw_to<TC>(Pp[oC]),
-                                                   pw_to<TC>(Pp[oC + KB]), pw_to<TC>(Pp[oC + 2 * KB]),
-                                                   pw_to<TC>(Pp[oC + 3 * KB]), true, true);
+                TC a0, a1, e0, e1, f0, f1, h0, h1, q0, q1;
+                pw_tvd_ld2<TS, TC>(Pp + oC, a0, a1);
+                pw_tvd_ld2<TS, TC>(Pp + oC + KB, e0, e1);
+                pw_tvd_ld2<TS, TC>(Pp + oC + 2 * KB, f0, f1);
+                pw_tvd_ld2<TS, TC>(Pp + oC + 3 * KB, h0, h1);
+                pw_tvd_ld2<TS, TC>(Pv + oC + KB, q0, q1);
+                Gy[TJ * KC + 2 * t] = pw_tvd_flux<TC>(q0, cfy, cfy, a0, e0, f0, h0, true, true);
+                Gy[TJ * KC + 2 * t + 1] = pw_tvd_flux<TC>(q1, cfy, cfy, a1, e1, f1, h1, true, true);
             } else if (roleC == 2) {
-                Gz[rC * (KC + 1) + KC] =
-                    zC ? pw_tvd_flux<TC>(pw_to<TC>(Pw[oC + 1]), cfCp, cfCn, pw_to<TC>(Pp[oC]), pw_to<TC>(Pp[oC + 1]),
-                                         pw_to<TC>(Pp[oC + 2]), pw_to<TC>(Pp[oC + 3]), true, farCn)
-                       : TC(0);
+                TC a0, a1, e0, e1, q0, q1;  // levels KT-1 .. KT+2 and w(KT)
+                pw_tvd_ld2<TS, TC>(Pp + oC, a0, a1);
+                pw_tvd_ld2<TS, TC>(Pp + oC + 2, e0, e1);
+                pw_tvd_ld2<TS, TC>(Pw + oC, q0, q1);
+                Gz[rC * (KC + 1) + KC] = zC ? pw_tvd_flux<TC>(q1, cfCp, cfCn, a0, a1, e0, e1, true, farCn) : TC(0);
             }
-            Gy[tr * KC + tl] = GA;
-            Gz[tr * (KC + 1) + tl] = GB;
+            Gy[tr * KC + 2 * t] = GA[0];
+            Gy[tr * KC + 2 * t + 1] = GA[1];
+            Gz[tr * (KC + 1) + 2 * t] = GB[0];
+            Gz[tr * (KC + 1) + 2 * t + 1] = GB[1];
         }
         // own values of the newest plane
-        ph[0] = ph[1];
-        ph[1] = ph[2];
-        ph[2] = ph[3];
-        ph[3] = pC;
-        uw[0] = uw[1];
-        uw[1] = uw[2];
-        uw[2] = pw_to<TC>(Pu[own]);
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            ph[0][m] = ph[1][m];
+            ph[1][m] = ph[2][m];
+            ph[2][m] = ph[3][m];
+            uw[0][m] = uw[1][m];
+            uw[1][m] = uw[2][m];
+        }
+        ph[3][0] = c0v;
+        ph[3][1] = c1v;
+        pw_tvd_ld2<TS, TC>(Pu + own, uw[2][0], uw[2][1]);
         if (!__syncthreads_and(ok)) {
             give_up(p);
             return;
@@ -236,29 +321,31 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
             issue(p + NS);
             issued = p + NS + 1;
         }
-        TC D = TC(0);
-        if (faces) D = (GA - Gy[(tr + 1) * KC + tl]) * rdy + fz1 * GB - fz2 * Gz[tr * (KC + 1) + tl + 1];
-        if (p >= 3) {
-            // x face between columns c = i0+p-4 and c+1: phi(c-1 .. c+2), u(c)
-            const TC Gx = pw_tvd_flux<TC>(uw[0], cfx, cfx, ph[0], ph[1], ph[2], ph[3], true, true);
-            if (p >= 4 && active) {
-                const int i = i0 + p - 4;
-                const TC s = (Gx_w - Gx) * rdx + D2;
-                TO *o = out + (long long)(i + 2) * g.si + (long long)(j + 2) * g.sj + k;
-                if (beta) {
-                    if constexpr (std::is_same<TO, __nv_bfloat16>::value)
-                        *o = __float2bfloat16_rn(__bfloat162float(*o) + (float)s);
-                    else
-                        *o = *o + (TO)s;
-                } else {
-                    if constexpr (std::is_same<TO, __nv_bfloat16>::value) *o = __float2bfloat16_rn((float)s);
-                    else *o = (TO)s;
-                }
-            }
-            Gx_w = Gx;
+        TC D[2] = {};
+        if (faces) {
+            D[0] = (GA[0] - Gy[(tr + 1) * KC + 2 * t]) * rdy + fz1[0] * GB[0] - fz2[0] * GB[1];
+            D[1] = (GA[1] - Gy[(tr + 1) * KC + 2 * t + 1]) * rdy + fz1[1] * GB[1] -
+                   fz2[1] * Gz[tr * (KC + 1) + 2 * t + 2];
         }
-        D2 = D1;
-        D1 = D;
+        if (p >= 3) {
+            // x faces between columns c = i0+p-4 and c+1: phi(c-1 .. c+2), u(c)
+            TC Gx[2];
+#pragma unroll
+            for (int m = 0; m < 2; m++)
+                Gx[m] = pw_tvd_flux<TC>(uw[0][m], cfx, cfx, ph[0][m], ph[1][m], ph[2][m], ph[3][m], true, true);
+            if (p >= 4) {
+                if (act0) pw_tvd_st2<TO, TC>(o, (Gx_w[0] - Gx[0]) * rdx + D2[0], (Gx_w[1] - Gx[1]) * rdx + D2[1],
+                                             two, beta);
+                o += g.si;
+            }
+            Gx_w[0] = Gx[0];
+            Gx_w[1] = Gx[1];
+        }
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            D2[m] = D1[m];
+            D1[m] = D[m];
+        }
     }
     __syncthreads();
     if (tid == 0)
@@ -289,7 +376,8 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
     g.rdy = 1.0 / m->dy;
     g.dt = dt;
     const size_t smem = (size_t)NS * 4 * SH::FS * sizeof(TS) +
-                        (size_t)2 * ((TJ + 1) * KC + TJ * (KC + 1)) * sizeof(TC) + NS * sizeof(uint64_t);
+                        (size_t)2 * ((TJ + 1) * KC + TJ * (KC + 1)) * sizeof(TC) +
+                        ((KC + 2) * sizeof(TC) + 15) / 16 * 16 + NS * sizeof(uint64_t);
     if (smem > 226 * 1024) return pw_fail(PW_ERR_SHAPE, "tvd: %zu bytes of shared memory", smem);
     CUtensorMap maps[3];
     const void *f[3] = {u, v, w};
@@ -308,12 +396,12 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
     auto kern = pw_tvd_march<TS, TC, TO, TJ>;
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // a CTA marches ti columns from ti + 4 planes
-    g.ti = pw_pick_tile_i(m, tile_i, tiles, pw_slots(m, kern, TJ * KC, smem), 4);
+    g.ti = pw_pick_tile_i(m, tile_i, tiles, pw_slots(m, kern, TJ * KC / 2, smem), 4);
     // the scalar and the k chunk are the fastest grid indices: the CTAs of one
     // tile run together and share the wind and the k-halo levels through L2
     dim3 grid((unsigned)(g.nkc * n), (unsigned)((m->ny + TJ - 1) / TJ), (unsigned)((m->nx + g.ti - 1) / g.ti));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "tvd: grid too large");
-    kern<<<grid, TJ * KC, smem, st>>>(maps[0], maps[1], maps[2], set, m->coef64, g, beta, m->status);
+    kern<<<grid, TJ * KC / 2, smem, st>>>(maps[0], maps[1], maps[2], set, m->coef64, g, beta, m->status);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
 }
