@@ -278,7 +278,7 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     auto kern = pw_scalar_march<TS, TC, TO, KV, NS, PW_SCALAR_GMAX, STEP>;
     PW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long ngroups = (n + group - 1) / group;
-    // as in the FP64 scalar kernel, the grid keeps the fill rule
+    // the fill rule (the wave rule measured no faster on these many-wave grids)
     tile_i = pw_fit_tile_i(m, tile_i, (long)((m->ny + tile_j - 1) / tile_j) * sg.nkc);
     g.ti = tile_i;
     dim3 grid((unsigned)((m->ny + tile_j - 1) / tile_j), (unsigned)((m->nx + tile_i - 1) / tile_i),
