@@ -1,7 +1,7 @@
 """Seeded randomized parity sweep: random domain shapes (including 1-wide and
 non-multiple-of-tile sizes), random tile shapes and every arithmetic path, for
-the wind stencil, the scalars and the fused step, each against the FP64
-oracle on the same inputs."""
+the wind stencil, the scalars, the fused step and ULTIMATE-QUICKEST (random
+steps and wind directions), each against the FP64 oracle on the same inputs."""
 import numpy as np
 import pytest
 import torch
@@ -121,3 +121,35 @@ def test_too_tall_column_rejected(pw):
     from paper_2009_12850_b300 import _lib as L
     with pytest.raises(L.PWError):
         pw.Mesh(4, 4, L.PW_MAX_NZ + 1, 50.0, dtype="f32")
+
+
+# FP32 ULTIMATE-QUICKEST: the bound of test_gpu_tvd.py (a face's rounding, then
+# the six flux terms, within 32 units of 2^-24 of the condition sum)
+TOL_TVD_F32 = 32 * 2.0 ** -24
+
+
+@pytest.mark.parametrize("case", cases(10, 2026), ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}_t{c[3][0]}-{c[3][1]}")
+@pytest.mark.parametrize("dtype,algo", KINDS)
+def test_random_tvd(pw, case, dtype, algo):
+    """ULTIMATE-QUICKEST on random shapes and tiles, with a random step (Courant
+    numbers from near 0 to above 1) and winds of both signs, several scalars."""
+    nx, ny, nz, tile, dx, dy, seed = case
+    m = pw.Mesh(nx, ny, nz, dx, dy, dtype=dtype, algo=algo)
+    m.set_tile(min(tile[0], 8), tile[1])
+    rng = np.random.default_rng(seed)
+    u, v, w = synthetic.wind_fields(nx, ny, nz, seed, u_mean=float(rng.uniform(-6, 6)),
+                                    v_mean=float(rng.uniform(-6, 6)), u_std=3.0, v_std=3.0, w_std=1.0)
+    f = rounded([u, v, w], dtype)
+    n = 1 + seed % 4
+    phis = rounded(synthetic.scalar_fields(nx, ny, nz, n, seed + 1), dtype)
+    dt = float(rng.uniform(0.05, 1.3) * min(dx, dy) / 8.0)
+    U = [m.from_interior(a) for a in f]
+    P = [m.from_interior(a) for a in phis]
+    S = m.advect_tvd(*U, P, dt)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    c = oracle.Coeffs(nz, dx, dy)
+    t = TOL_F64 if dtype == "f64" else TOL_TVD_F32
+    for q, phi in enumerate(phis):
+        ref, cond = oracle.advect_tvd(c, *f, phi, dt, want_cond=True)
+        compare(f"t{q}", m.interior(S[q]).double().cpu().numpy(), ref, cond, t if dtype == "f64" else 1e-5, t)
