@@ -121,12 +121,19 @@ __device__ __forceinline__ void pw_store(TO *p, const TO (&r)[KV], int nvalid, i
             *reinterpret_cast<V8 *>(p) = val;
         } else {
 #pragma unroll
-            for (int m = 0; m < KV; m++) p[m] = beta ? p[m] + r[m] : r[m];
+            for (int m = 0; m < KV; m++) p[m] = beta ? TO(p[m] + r[m]) : r[m];
         }
     } else {
+        // the top of the column: the stored values are read only when accumulating
+        if (beta) {
 #pragma unroll
-        for (int m = 0; m < KV; m++)
-            if (m < nvalid) p[m] = beta ? p[m] + r[m] : r[m];
+            for (int m = 0; m < KV; m++)
+                if (m < nvalid) p[m] = p[m] + r[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < KV; m++)
+                if (m < nvalid) p[m] = r[m];
+        }
     }
 }
 

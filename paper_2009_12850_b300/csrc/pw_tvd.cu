@@ -50,6 +50,7 @@ struct PwTvdGeom {
     double dtdx, dtdy; // dt/dx, dt/dy
     double rdx, rdy;   // 1/dx, 1/dy
     double dt;
+    float fdtdx, fdtdy, frdx, frdy, fdt;  // the same rounded to FP32 on the host (FP32 kernels)
 };
 
 struct PwTvdSet {
@@ -118,22 +119,30 @@ __device__ __forceinline__ void pw_tvd_ld2(const TS *p, TC &a, TC &b) {
 template <typename TO, typename TC>
 __device__ __forceinline__ void pw_tvd_st2(TO *o, TC s0, TC s1, bool two, int beta) {
     if constexpr (std::is_same<TO, __nv_bfloat16>::value) {
-        const float a = beta ? __bfloat162float(o[0]) + (float)s0 : (float)s0;
-        if (two) {
-            const float b = beta ? __bfloat162float(o[1]) + (float)s1 : (float)s1;
-            *reinterpret_cast<__nv_bfloat162 *>(o) = __floats2bfloat162_rn(a, b);
-        } else {
-            o[0] = __float2bfloat16_rn(a);
+        float a = (float)s0, b = (float)s1;
+        if (beta) {  // the stored values are read only when accumulating
+            a += __bfloat162float(o[0]);
+            if (two) b += __bfloat162float(o[1]);
         }
+        if (two) *reinterpret_cast<__nv_bfloat162 *>(o) = __floats2bfloat162_rn(a, b);
+        else o[0] = __float2bfloat16_rn(a);
     } else {
         using V = typename std::conditional<sizeof(TO) == 8, double2, float2>::type;
         if (two) {
-            V v = *reinterpret_cast<const V *>(o);
-            v.x = beta ? v.x + (TO)s0 : (TO)s0;
-            v.y = beta ? v.y + (TO)s1 : (TO)s1;
+            V v;
+            if (beta) {  // the stored values are read only when accumulating
+                v = *reinterpret_cast<const V *>(o);
+                v.x += (TO)s0;
+                v.y += (TO)s1;
+            } else {
+                v.x = (TO)s0;
+                v.y = (TO)s1;
+            }
             *reinterpret_cast<V *>(o) = v;
         } else {
-            o[0] = beta ? o[0] + (TO)s0 : (TO)s0;
+            TO a = (TO)s0;
+            if (beta) a += o[0];
+            o[0] = a;
         }
     }
 }
@@ -154,7 +163,8 @@ template <typename TS, typename TC, typename TO, int TJ>
 __global__ void __launch_bounds__(TJ * PW_TVD_KC / 2)
 pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mv,
              const __grid_constant__ CUtensorMap mw, const __grid_constant__ PwTvdSet set,
-             const double *__restrict__ coef64, const PwTvdGeom g, int beta, int *__restrict__ status) {
+             const double *__restrict__ coef64, const float *__restrict__ coef32, const PwTvdGeom g, int beta,
+             int *__restrict__ status) {
     constexpr int KC = PW_TVD_KC, NS = PW_TVD_NS, ROWS = TJ + 4, HK = KC / 2;
     using SH = PwTvdShape<TS, TJ>;
     constexpr int H = SH::H, KB = SH::KB, FS = SH::FS;
@@ -187,7 +197,12 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
     }
     for (int q = tid; q < KC + 2; q += nt) {
         const int K = k0 - 1 + q;
-        cft[q] = (K >= 0 && K < g.nz) ? (TC)(g.dt / coef64[K]) : TC(0);
+        // FP32 kernels: one conversion and an FP32 quotient (the FP64 units
+        // are slow enough that an FP64 quotient per entry shows in the profile)
+        if constexpr (std::is_same<TC, float>::value)
+            cft[q] = (K >= 0 && K < g.nz) ? g.fdt / (float)coef64[K] : 0.0f;
+        else
+            cft[q] = (K >= 0 && K < g.nz) ? (TC)(g.dt / coef64[K]) : TC(0);
     }
     __syncthreads();
 
@@ -215,13 +230,30 @@ pw_tvd_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUt
         }
     };
 
-    const TC cfx = (TC)g.dtdx, cfy = (TC)g.dtdy, rdx = (TC)g.rdx, rdy = (TC)g.rdy;
+    TC cfx, cfy, rdx, rdy;
+    if constexpr (std::is_same<TC, float>::value) {
+        cfx = g.fdtdx;
+        cfy = g.fdtdy;
+        rdx = g.frdx;
+        rdy = g.frdy;
+    } else {
+        cfx = g.dtdx;
+        cfy = g.dtdy;
+        rdx = g.rdx;
+        rdy = g.rdy;
+    }
     TC fz1[2], fz2[2];
 #pragma unroll
     for (int m = 0; m < 2; m++) {
         const int kk = k + m;
-        fz1[m] = (kk > 0 && kk < g.nz) ? (TC)(4.0 * coef64[6 * g.nz + kk]) : TC(0);
-        fz2[m] = (kk < g.nz - 1) ? (TC)(4.0 * coef64[7 * g.nz + kk]) : TC(0);
+        // 4 tzc1, 4 tzc2 (scaling by 4 is exact): the FP32 copies for the FP32 kernels
+        if constexpr (std::is_same<TC, float>::value) {
+            fz1[m] = (kk > 0 && kk < g.nz) ? 4.0f * coef32[kk] : 0.0f;
+            fz2[m] = (kk < g.nz - 1) ? 4.0f * coef32[g.nz + kk] : 0.0f;
+        } else {
+            fz1[m] = (kk > 0 && kk < g.nz) ? 4.0 * coef64[6 * g.nz + kk] : 0.0;
+            fz2[m] = (kk < g.nz - 1) ? 4.0 * coef64[7 * g.nz + kk] : 0.0;
+        }
     }
     // B faces: below level k (K = k-1) and below level k+1 (K = k)
     const bool zB0 = k >= 1 && k < g.nz, zB1 = k + 1 < g.nz;
@@ -375,6 +407,11 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
     g.rdx = 1.0 / m->dx;
     g.rdy = 1.0 / m->dy;
     g.dt = dt;
+    g.fdtdx = (float)g.dtdx;
+    g.fdtdy = (float)g.dtdy;
+    g.frdx = (float)g.rdx;
+    g.frdy = (float)g.rdy;
+    g.fdt = (float)dt;
     const size_t smem = (size_t)NS * 4 * SH::FS * sizeof(TS) +
                         (size_t)2 * ((TJ + 1) * KC + TJ * (KC + 1)) * sizeof(TC) +
                         ((KC + 2) * sizeof(TC) + 15) / 16 * 16 + NS * sizeof(uint64_t);
@@ -401,7 +438,8 @@ static pw_status pw_launch_tvd_t(const pw_mesh *m, const void *u, const void *v,
     // tile run together and share the wind and the k-halo levels through L2
     dim3 grid((unsigned)(g.nkc * n), (unsigned)((m->ny + TJ - 1) / TJ), (unsigned)((m->nx + g.ti - 1) / g.ti));
     if (grid.y > 65535 || grid.z > 65535) return pw_fail(PW_ERR_SHAPE, "tvd: grid too large");
-    kern<<<grid, TJ * KC / 2, smem, st>>>(maps[0], maps[1], maps[2], set, m->coef64, g, beta, m->status);
+    kern<<<grid, TJ * KC / 2, smem, st>>>(maps[0], maps[1], maps[2], set, m->coef64, m->coef32, g, beta,
+                                          m->status);
     PW_CUDA(cudaGetLastError());
     return PW_OK;
 }

@@ -311,8 +311,9 @@ pw_tvd_split_march(const __grid_constant__ CUtensorMap mu, const __grid_constant
             const DF Gx = pw_tvds_flux(uw[0], cfx, cfx, ph[0], ph[1], ph[2], ph[3], true, true, bad);
             if (p >= 4 && active) {
                 const DF s = dfs_add(dfs_mul(dfs_sub(Gx_w, Gx), rdx), D2);
-                const double r = join(s.h, s.l);
-                *o = beta ? *o + r : r;
+                double r = join(s.h, s.l);
+                if (beta) r += *o;  // the stored value is read only when accumulating
+                *o = r;
             }
             if (p >= 4) o += g.si;
             Gx_w = Gx;
