@@ -263,22 +263,17 @@ pw_adjoint_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_con
         const double *ins[3] = {yu, yv, yw};
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            // y and the stored gradient are read only when asked for (add_y, beta)
             if (oka) {
                 const long long o = off + ka;
-                double r = alpha * ga[c];
-                if (add_y) r += ins[c][o];
+                double r = alpha * ga[c] + (add_y ? ins[c][o] : 0.0);
                 if (c == 2 && ka >= g.nz - 1) r = 0.0;  // the lid face is not a degree of freedom
-                if (beta) r += outs[c][o];
-                outs[c][o] = r;
+                outs[c][o] = beta ? outs[c][o] + r : r;
             }
             if (okz) {
                 const long long o = off + kz;
-                double r = alpha * gz[c];
-                if (add_y) r += ins[c][o];
+                double r = alpha * gz[c] + (add_y ? ins[c][o] : 0.0);
                 if (c == 2 && kz >= g.nz - 1) r = 0.0;
-                if (beta) r += outs[c][o];
-                outs[c][o] = r;
+                outs[c][o] = beta ? outs[c][o] + r : r;
             }
         }
     }

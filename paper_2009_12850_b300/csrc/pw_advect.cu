@@ -72,6 +72,8 @@ static pw_status pw_launch_march(const pw_mesh *m, const void *u, const void *v,
     g.sj = m->sj;
     g.tcx = m->tcx;
     g.tcy = m->tcy;
+    g.ftcx = (float)m->tcx;
+    g.ftcy = (float)m->tcy;
     int threads = (g.kc / KV) * tile_j;
     if (threads > 512)
         return pw_fail(PW_ERR_SHAPE, "tile_j=%d needs %d threads (> 512) for k chunk %d", tile_j,

@@ -154,6 +154,8 @@ static PwGeom pw_member_geom(const pw_mesh *m, int threads, int tile_i) {
     g.sj = m->sj;
     g.tcx = m->tcx;
     g.tcy = m->tcy;
+    g.ftcx = (float)m->tcx;
+    g.ftcy = (float)m->tcy;
     return g;
 }
 

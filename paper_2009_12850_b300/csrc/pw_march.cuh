@@ -32,7 +32,16 @@ struct PwGeom {
     int plane_elems;   // (tj + 2) * kb
     long long si, sj;  // strides of the sources (elements)
     double tcx, tcy;
+    float ftcx, ftcy;  // the same rounded to FP32 on the host (the FP32 kernels take these)
 };
+
+// a host-supplied constant in the compute type: FP32 kernels take the FP32
+// copy, so no thread spends FP64 conversions on it
+template <typename TC>
+__device__ __forceinline__ TC pw_geom_c(double d, float f) {
+    if constexpr (std::is_same<TC, float>::value) return f;
+    else return (TC)d;
+}
 
 // --------------------------------------------------------------------------
 // slab loads from shared memory: KV values at [kk, kk+KV) plus optional
@@ -278,7 +287,7 @@ __device__ __forceinline__ bool pw_march_tile(const CUtensorMap *mu_, const CUte
         d1[m] = in ? coef[2 * g.nz + k] : TC(0);
         d2[m] = in ? coef[3 * g.nz + k] : TC(0);
     }
-    const TC tcx = (TC)g.tcx, tcy = (TC)g.tcy;
+    const TC tcx = pw_geom_c<TC>(g.tcx, g.ftcx), tcy = pw_geom_c<TC>(g.tcy, g.ftcy);
     const TC tdt = (TC)dt;
     const int L = g.kb;
     const int rS = tjc * L, rC = (tjc + 1) * L, rN = (tjc + 2) * L;

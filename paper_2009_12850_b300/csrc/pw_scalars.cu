@@ -126,7 +126,7 @@ pw_scalar_march(const __grid_constant__ CUtensorMap mu, const __grid_constant__ 
         c1[m] = in ? TC(2) * coef[k] : TC(0);
         c2[m] = in ? TC(2) * coef[g.nz + k] : TC(0);
     }
-    const TC hx = TC(2) * (TC)g.tcx, hy = TC(2) * (TC)g.tcy;
+    const TC hx = TC(2) * pw_geom_c<TC>(g.tcx, g.ftcx), hy = TC(2) * pw_geom_c<TC>(g.tcy, g.ftcy);
     const TC tdt = (TC)dt;
     const int L = g.kb;
     const int rS = tjc * L, rC = (tjc + 1) * L, rN = (tjc + 2) * L;
@@ -240,6 +240,8 @@ static pw_status pw_launch_scalars(const pw_mesh *m, const void *u, const void *
     g.sj = m->sj;
     g.tcx = m->tcx;
     g.tcy = m->tcy;
+    g.ftcx = (float)m->tcx;
+    g.ftcy = (float)m->tcy;
     const int threads = (g.kc / KV) * tile_j;
     if (threads > 512)
         return pw_fail(PW_ERR_SHAPE, "scalars: tile_j=%d needs %d threads (> 512)", tile_j, threads);
