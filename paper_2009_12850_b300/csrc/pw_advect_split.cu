@@ -18,13 +18,14 @@
 // Pipeline per x step: TMA brings the (j,k) plane of u, v, w (doubles, rows
 // j0-1 .. j0+TJ, levels k0-2 .. k0+KC+1; levels >= nz and the w lid arrive as
 // zeros because the tensor maps carry the logical k extent) into the raw slot;
-// after a barrier (the oldest converted plane is no longer read) all threads
-// convert it, with integer bit operations, into a ring of three converted
-// planes whose 16-byte chunk q of a row holds (hi, hi, lo, lo) of levels
-// (k0 + q - 1, k0 + q - 1 + KC/2); after a second barrier the raw slot takes
-// the next plane (its copy runs during the arithmetic) and the threads compute
-// column i from converted planes i-1, i, i+1.  One raw slot and three
-// converted planes (35 KB for the 8 x 32 tile) let five CTAs share an SM.
+// all threads convert it, with integer bit operations, into a ring of four
+// converted planes whose 16-byte chunk q of a row holds (hi, hi, lo, lo) of
+// levels (k0 + q - 1, k0 + q - 1 + KC/2); after the step's one barrier the raw
+// slot takes the next plane (its copy runs during the arithmetic) and the
+// threads compute column i from converted planes i-1, i, i+1 (the fourth is
+// the one the next step writes, so no barrier is needed before converting).
+// One raw slot and four converted planes (44 KB for the 8 x 32 tile) let five
+// CTAs share an SM.
 //
 // The algebra: s = tcx X + tcy Y + Z with X, Y differences of products of a
 // field value and a face sum, and Z = phi(k-1) (A(k-1) c1) - phi(k+1) (A(k) c2)
@@ -49,7 +50,7 @@ struct PwSplitGeom {
 };
 
 #define PW_SPLIT_RAW 1   // raw TMA slots
-#define PW_SPLIT_CONV 3  // converted planes (i-1, i, i+1)
+#define PW_SPLIT_CONV 4  // converted planes (i-1, i, i+1 and the one being written)
 
 // one level pair (a, b) of a converted row as hi and lo pairs
 __device__ __forceinline__ D2 pw_ldc(const float4 *row, int q) {
@@ -229,13 +230,15 @@ pw_advect_split_kernel(const __grid_constant__ CUtensorMap mu, const __grid_cons
     D2 Fx_m, Gx_m, Hx_m;  // x face sums of column i-1|i, carried along the march
     for (int p = 0; p < nplanes; p++) {
         const bool ok = pw_mbar_wait_bounded(&bars[p % PW_SPLIT_RAW], (uint32_t)((p / PW_SPLIT_RAW) & 1));
+        if (ok) convert(p);
+        // one barrier per step: plane p is published and its raw slot free, and
+        // every thread is past step p-1, so the converted plane the next step
+        // overwrites (p-3) is no longer read
         if (!__syncthreads_and(ok)) {
             give_up(p);
             return;
         }
-        convert(p);
-        __syncthreads();
-        // every thread has converted plane p: its raw slot takes plane p + 2
+        // every thread has converted plane p: its raw slot takes plane p + 1
         if (tid == 0 && p + PW_SPLIT_RAW < nplanes) {
             issue(p + PW_SPLIT_RAW);
             issued = p + PW_SPLIT_RAW + 1;
