@@ -79,7 +79,7 @@ def run_bench_config(pw, wl, fields, dtype, algo):
 
 
 CASES = [("bandwidth", "f64", "auto"), ("bandwidth", "f64", "native"), ("bandwidth", "f32", "auto"),
-         ("bandwidth", "bf16", "auto"), ("precision", "f64", "auto"), ("precision", "f32", "auto"),
+         ("bandwidth", "bf16", "auto"), ("bandwidth", "bf16_out", "auto"), ("precision", "f64", "auto"), ("precision", "f32", "auto"),
          ("precision", "bf16", "auto"), ("precision", "bf16_out", "auto")]
 
 
