@@ -2,8 +2,8 @@
 positivity-preserving scheme named in section 3.1) through the C-ABI against the
 FP64 oracle: every storage kind, ragged shapes, Courant numbers below and above
 1, many scalars, tiles, accumulation, the lid, untouched halos, argument checks,
-the scheme's own properties on the device, and every point of a full
-1024x1024x128 launch."""
+the scheme's own properties on the device, and every point of theta + 5 q on a
+full 1024x1024x128 launch."""
 import numpy as np
 import pytest
 import torch
@@ -242,20 +242,33 @@ def test_tvd_argument_errors(pw):
     assert m.device_status() == 0
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32"])
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32", "bf16"])
 def test_tvd_full_size_every_point(pw, dtype):
-    """θ on the 1024x1024x128 bandwidth workload (dx 25 m, dt 2 s) in the
-    launch configuration the benchmark times: every point against the oracle."""
-    nx, ny, nz = 1024, 1024, 128
-    dt = 2.0
-    m = mesh(pw, nx, ny, nz, 25.0, dtype=dtype)
-    wind = rounded(synthetic.wind_fields(nx, ny, nz, 1234 + 1), dtype)
-    phi = rounded([synthetic.scalar_fields(nx, ny, nz, 1, 1234 + 101)[0]], dtype)[0]
-    got = run_tvd(m, wind, [phi], dt)[0]
-    c = oracle.Coeffs(nz, 25.0, 25.0)
-    ref, cond = oracle.advect_tvd(c, *wind, phi, dt, want_cond=True)
+    """theta + 5 q on the 1024x1024x128 bandwidth workload (dx 25 m, dt 2 s) in the
+    launch configuration the benchmark times (all six scalars in one call): every
+    point of every scalar against the oracle (all host cores)."""
+    oracle.set_threads(0)
+    wl = synthetic.LARGE
+    nx, ny, nz, dt = wl.nx, wl.ny, wl.nz, 2.0
+    m = mesh(pw, nx, ny, nz, wl.dx, wl.dy, dtype=dtype)
+    wind = rounded(synthetic.fields_for(wl), dtype)
+    phis = synthetic.scalar_fields(nx, ny, nz, 6, wl.seed + 100)
+    for q in range(len(phis)):   # one at a time: each field is 1 GB in FP64
+        phis[q] = rounded([phis[q]], dtype)[0]
+    U = [m.from_interior(a) for a in wind]
+    P = [m.from_interior(a) for a in phis]
+    S = [m.empty_out() for _ in phis]
+    m.advect_tvd(*U, P, dt, S)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    del U, P
+    c = oracle.Coeffs(nz, wl.dx, wl.dy)
     tn, tc = tolerances(dtype)
-    compare_slabs("theta", got, ref, cond, tn, tc)
+    for q in range(len(phis)):
+        ref, cond = oracle.advect_tvd(c, *wind, phis[q], dt, want_cond=True)
+        got = m.interior(S[q]).double().cpu().numpy()
+        compare_slabs(f"s{q}", got, ref, cond, tn, tc)
+        del ref, cond, got
 
 
 def test_tvd_split_range_is_reported(pw):
